@@ -1,0 +1,332 @@
+"""Benchmark: batched fast Hankel tensor-vector products on GB300.
+
+Workload (one step): 8192 independent square real Hankel tensors, order m
+uniform in {3,4,5}, dimension n uniform in [16,1024], h ~ N(0,1/d),
+x unit-norm Gaussian, FP32 (twiddles generated in FP64), y = H x^{m-1} for
+every tensor in one hankel_txv() call.  Inputs are resident in HBM; each
+timed step uses the next of several input copies (together > 4x L2) so the
+step reads HBM, not L2.
+
+Reported (one JSON line on rank 0):
+  value        products/s over all ranks (device-timed, CUDA events)
+  e2e          the same through hankel_txv_host() with pinned host buffers
+               (H2D of h, x and D2H of y inside the timed region)
+  roofline     algorithmic bytes 4*(d + 2n) per tensor / step time vs the
+               measured HBM copy bandwidth
+  fp64_plain   the plain FP64 path, one tensor per kernel launch, and the
+               FP32/FP64 output agreement
+  cpu_baseline the FP64 oracle on the host cores over a bounded sample
+--impl reference times the FP64 oracle alone (the CPU arm).
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "H·x^{m-1} products/s and % HBM roofline, batched FP32 vs plain FP64, same error"
+WORKLOAD = {"workload": "batched square real Hankel tensors, FP32",
+            "tensors": 8192, "orders": [3, 4, 5], "n_range": [16, 1024],
+            "h": "N(0,1/d)", "x": "unit-norm Gaussian", "product": "y = H x^{m-1}"}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+_BATCH = {}
+
+
+def oracle_sample_worker(args):
+    lo, hi, seed = args
+    import oracle
+    from paper_1401_6238_gb300 import workloads as wl
+    if seed not in _BATCH:
+        _BATCH[seed] = wl.batched_square(count=8192, seed=seed)
+    b = _BATCH[seed]
+    for i in range(lo, hi):
+        m, n, h, x = b.tensor(i)
+        oracle.fast_y(h, [x] * (m - 1), [n] * m)
+    return hi - lo
+
+
+def cpu_oracle(seconds=12.0, seed=1, pool=None, cores=1):
+    """Time the FP64 oracle (own radix-2 FFT embedding) on the host cores over
+    a bounded sample of the workload; returns products/s."""
+    chunk = 16
+    done = 0
+    t0 = time.perf_counter()
+    nxt = 0
+    while time.perf_counter() - t0 < seconds and nxt < 8192:
+        tasks = []
+        for _ in range(cores):
+            if nxt >= 8192:
+                break
+            tasks.append((nxt, min(8192, nxt + chunk), seed))
+            nxt += chunk
+        if pool is not None:
+            done += sum(pool.map(oracle_sample_worker, tasks))
+        else:
+            done += sum(oracle_sample_worker(t) for t in tasks)
+    dt = time.perf_counter() - t0
+    return done / dt, done, dt
+
+
+def start_clock_sampler(path):
+    try:
+        return subprocess.Popen(
+            ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+             "--format=csv,noheader,nounits", "-lms", "200"],
+            stdout=open(path, "w"), stderr=subprocess.DEVNULL)
+    except Exception:
+        return None
+
+
+def read_clocks(path, proc, gpu_index):
+    if proc is None:
+        return None
+    proc.terminate()
+    try:
+        proc.wait(timeout=5)
+    except Exception:
+        proc.kill()
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    try:
+        for line in open(path):
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9 or f[0] != str(gpu_index):
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+    except OSError:
+        return None
+    if not sm:
+        return None
+    return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        per_step = max(5.0, 60.0 / max(1, args.steps + args.warmup))
+        for _ in range(args.warmup):
+            cpu_oracle(seconds=min(per_step, 5.0), pool=pool, cores=cores)
+        vals = []
+        for _ in range(args.steps):
+            v, n, dt = cpu_oracle(seconds=per_step, pool=pool, cores=cores)
+            vals.append((v, n, dt))
+    value = float(np.mean([v[0] for v in vals]))
+    total_n = sum(v[1] for v in vals)
+    ms = 1000.0 * 8192 / value
+    line = {"metric": METRIC, "value": value, "unit": "products/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": dict(WORKLOAD),
+            "cpu_baseline": {"value": value, "unit": "products/s", "cores": cores, "kind": "oracle",
+                             "sample": "%d tensors of the 8192-tensor workload (FP64 radix-2 embedding FFT, "
+                                       "spawn pool of %d processes), %d steps" % (total_n, cores, args.steps)},
+            "e2e": {"value": value, "unit": "products/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--copies", type=int, default=6)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    # the CPU baseline's process pool starts before the first GPU call
+    pool = None
+    cores = os.cpu_count() or 1
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import multiprocessing as mp
+        pool = mp.get_context("spawn").Pool(cores)
+
+    import torch
+    from paper_1401_6238_gb300 import hankel as hk
+    from paper_1401_6238_gb300 import workloads as wl
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    # each rank processes its own full batch (weak scaling: fixed work per GPU)
+    batch = wl.batched_square(count=8192, seed=1 + rank)
+    descs = hk.batch_descs(batch)
+    plan = hk.Plan(descs, hk.R32, hk.SAME_X)
+    info = plan.info
+    copies = max(2, args.copies)
+    Hs = [torch.tensor(batch.h, dtype=torch.float32, device=dev) for _ in range(copies)]
+    Xs = [torch.tensor(batch.x, dtype=torch.float32, device=dev) for _ in range(copies)]
+    Ys = [torch.zeros(batch.y_len, dtype=torch.float32, device=dev) for _ in range(copies)]
+    stream = torch.cuda.current_stream()
+
+    def step(i):
+        c = i % copies
+        plan.txv(Hs[c], Xs[c], Ys[c], None, stream)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk_path = os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks.csv"
+    sampler = start_clock_sampler(clk_path) if rank == 0 else None
+    time.sleep(0.3 if sampler else 0)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        step(args.warmup + i)
+        ev[i][1].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clocks = read_clocks(clk_path, sampler, local) if rank == 0 else None
+    total_ms = t_start.elapsed_time(t_end)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = total_ms / args.steps
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * len(batch) / (ms / 1000.0)
+
+    # roofline of the forward kernel: algorithmic bytes per step / kernel time
+    alg_bytes = float(sum(4 * (m * (n - 1) + 1 + 2 * n) for m, n in zip(batch.orders, batch.dims)))
+    peak, peak_src = peaks()
+    kernel_ms = float(np.mean(step_ms))
+    achieved = alg_bytes / (kernel_ms / 1000.0) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "real_fwd_traffic.json")
+    if os.path.exists(tpath):
+        try:
+            traffic = json.load(open(tpath)).get("bytes_per_step")
+        except Exception:
+            traffic = None
+
+    # end to end through the host-buffer entry point
+    hh = torch.tensor(batch.h, dtype=torch.float32).pin_memory()
+    xh = torch.tensor(batch.x, dtype=torch.float32).pin_memory()
+    yh = torch.zeros(batch.y_len, dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        plan.txv_host(hh, xh, yh, None, stream)
+    e2e_steps = max(3, args.steps // 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan.txv_host(hh, xh, yh, None, stream)
+    e2e_dt = (time.perf_counter() - t0) / e2e_steps
+    if dist:
+        t = torch.tensor([e2e_dt], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_dt = float(t.item())
+    e2e = {"value": world * len(batch) / e2e_dt, "unit": "products/s",
+           "h2d_bytes_per_step": int(hh.numel() * 4 + xh.numel() * 4), "d2h_bytes_per_step": int(yh.numel() * 4),
+           "ms_per_step": 1000.0 * e2e_dt}
+
+    # plain FP64 path: one tensor per launch, same tensors
+    fp64 = None
+    if not args.no_fp64 and rank == 0:
+        p64 = hk.Plan(descs, hk.R64, hk.SAME_X | hk.ONE_PER_LAUNCH)
+        H64 = torch.tensor(batch.h, dtype=torch.float64, device=dev)
+        X64 = torch.tensor(batch.x, dtype=torch.float64, device=dev)
+        Y64 = torch.zeros(batch.y_len, dtype=torch.float64, device=dev)
+        p64.txv(H64, X64, Y64, None, stream)
+        torch.cuda.synchronize()
+        reps = 2
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            p64.txv(H64, X64, Y64, None, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms64 = a.elapsed_time(b) / reps
+        # agreement of the two paths on the same tensors (per-tensor relative inf-norm)
+        y32 = Ys[(args.warmup + args.steps - 1) % copies].double().cpu().numpy()
+        y64 = Y64.cpu().numpy()
+        worst = 0.0
+        for i in range(len(batch)):
+            o, n = batch.y_off[i], batch.dims[i]
+            r = y64[o:o + n]
+            worst = max(worst, float(np.max(np.abs(y32[o:o + n] - r)) / np.max(np.abs(r))))
+        fp64 = {"value": len(batch) / (ms64 / 1000.0), "unit": "products/s", "ms_per_step": ms64,
+                "launches_per_step": int(p64.info["launches"]), "speedup_fp32_batched": (ms64 / ms),
+                "fp32_vs_fp64_max_rel_err": worst}
+        p64.close()
+
+    cpu = None
+    if pool is not None:
+        v, n, dt = cpu_oracle(seconds=15.0, pool=pool, cores=cores)
+        cpu = {"value": v, "unit": "products/s", "cores": cores, "kind": "oracle",
+               "sample": "first %d tensors of the same 8192-tensor batch, FP64 radix-2 embedding FFT, "
+                         "spawn pool of %d processes, %.1f s" % (n, cores, dt)}
+        pool.close()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "products/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": dict(WORKLOAD, l2="each step reads one of %d input copies (%.0f MB together, "
+                                            "> 4x L2)" % (copies, copies * (batch.h.nbytes + batch.x.nbytes) / 2e6),
+                               parallelism="replicas: each rank its own 8192-tensor batch"),
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": traffic,
+                             "peak_source": peak_src, "kernel": "real_fwd_kernel<float>",
+                             "algorithmic_bytes_per_step": alg_bytes},
+                "e2e": e2e, "gpu_launches": int(info["launches"]) * args.steps,
+                "plan": info, "fp64_plain": fp64, "cpu_baseline": cpu, "clocks": clocks,
+                "step_ms_min": float(np.min(step_ms)), "step_ms_median": float(np.median(step_ms))}
+        print(json.dumps(line))
+    plan.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

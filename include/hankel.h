@@ -1,0 +1,225 @@
+/*
+ * hankel.h -- C ABI of the GB300 (sm_103a) fast Hankel tensor-vector product
+ * library (libhankel.so).
+ *
+ * Method: Ding, Qi, Wei, "Fast Hankel Tensor-Vector Products and Application
+ * to Exponential Data Fitting".  An order-m Hankel tensor H of size
+ * n_1 x ... x n_m has entries H[i_1..i_m] = h[i_1 + ... + i_m] (0-based,
+ * Section 1) and is stored only through its generating vector h of length
+ * d = n_1 + ... + n_m - m + 1.  The library computes the two products of
+ * Section 3,
+ *
+ *     y     = H x_2 x_3 ... x_m      (length n_1)
+ *     alpha = H x_1 x_2 ... x_m      (scalar)
+ *
+ * with the mode product of Section 2.1 (no conjugation anywhere), by
+ * embedding H in an anti-circulant tensor (Theorem 2.1) of FFT length
+ * L >= d:  y = fft(ifft(h~) .* fft(x~_2) .* ... .* fft(x~_m))[0:n_1],
+ * alpha = ifft(h~)^T (fft(x~_1) .* ... .* fft(x~_m)).  The two-level block
+ * (BHHB) products of Section 3 use 2D FFTs of the zero-padded generating
+ * matrix.  Gradients (not in the paper) are the adjoint correlations.
+ *
+ * Conventions shared by every call:
+ *   - Element: one value of the plan's dtype (a real, or an interleaved
+ *     (re, im) pair for the complex dtypes).  Offsets count elements.
+ *   - Ownership: the caller owns every input and output buffer (device
+ *     memory unless the call says host).  A plan owns only its descriptor
+ *     tables, twiddle tables and workspace, all allocated in hankel_plan()
+ *     and freed in hankel_plan_destroy().
+ *   - Streams: compute calls are asynchronous on `stream` (a cudaStream_t;
+ *     NULL = legacy default stream).  They return once the work is queued.
+ *     One plan must not run on two streams at the same time (its workspace
+ *     is shared).
+ *   - Errors: every call returns a status; no exception or abort crosses
+ *     the ABI.  hankel_last_error() gives a message for the calling thread's
+ *     last failure.  Descriptor validation happens in hankel_plan(); compute
+ *     calls validate pointers only.
+ *   - Threads: distinct plans may be used from distinct host threads.
+ */
+#ifndef HANKEL_H
+#define HANKEL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HANKEL_MAX_ORDER 8
+
+typedef enum {
+    HANKEL_OK = 0,
+    HANKEL_EINVAL = 1,        /* bad argument or descriptor (message says which) */
+    HANKEL_ENOMEM = 2,        /* a device or host allocation failed */
+    HANKEL_ECUDA = 3,         /* a CUDA runtime call failed (message has its string) */
+    HANKEL_EUNSUPPORTED = 4,  /* valid request this build does not implement */
+    HANKEL_ETIMEOUT = 5       /* a bounded device-side wait gave up */
+} hankel_status;
+
+typedef enum {
+    HANKEL_R32 = 0,   /* float                       */
+    HANKEL_C64 = 1,   /* complex float  (re, im)     */
+    HANKEL_R64 = 2,   /* double                      */
+    HANKEL_C128 = 3   /* complex double (re, im)     */
+} hankel_dtype;
+
+/* Plan flags (bitwise OR). */
+enum {
+    /* One vector per tensor, x_off[0], used in every mode (the y = H x^{m-1}
+     * and alpha = H x^m products of Section 2.1).  Otherwise x_p is at
+     * x_off[p-1]. */
+    HANKEL_SAME_X = 1u << 0,
+    /* Form the spectrum power / product and the pointwise product with the
+     * h spectrum in FP64 even for the FP32 dtypes. */
+    HANKEL_FP64_POWER = 1u << 1,
+    /* hankel_txv() keeps the spectra it computes in plan workspace so that
+     * the next hankel_txv_backward() reuses them instead of recomputing. */
+    HANKEL_STORE_SPECTRA = 1u << 2,
+    /* Descriptors describe BHHB tensors (use N[]); calls go through
+     * hankel_txv_block(). */
+    HANKEL_BLOCK = 1u << 3,
+    /* Plain path: one tensor per kernel launch, no pairing or batching
+     * (the comparison baseline; meant for the FP64 dtypes). */
+    HANKEL_ONE_PER_LAUNCH = 1u << 4
+};
+
+/*
+ * One tensor of a batch.
+ *   m      order, 2 <= m <= HANKEL_MAX_ORDER.
+ *   n[p]   n_{p+1}: mode sizes (for BHHB: the block's mode sizes).
+ *   N[p]   N_{p+1}: number of blocks along mode p+1 (BHHB only; ignored and
+ *          treated as 1 otherwise).
+ *   h_off  offset of h (length d) in the h buffer; for BHHB the generating
+ *          matrix, (sum n - m + 1) x (sum N - m + 1), column-major
+ *          (Section 2.2).
+ *   x_off  offsets of x_1..x_m in the x buffer (only x_off[0] with
+ *          HANKEL_SAME_X).  x_1 is read only when alpha is requested.
+ *          BHHB: x_p = vec(X_p), X_p of size n_p x N_p column-major.
+ *   y_off  offset of y (n_1 elements; BHHB: n_1 x N_1 column-major).
+ * Descriptors may share h or x storage (the same offset); output regions
+ * must not overlap.
+ */
+typedef struct hankel_desc {
+    int32_t m;
+    int32_t n[HANKEL_MAX_ORDER];
+    int32_t N[HANKEL_MAX_ORDER];
+    int64_t h_off;
+    int64_t x_off[HANKEL_MAX_ORDER];
+    int64_t y_off;
+} hankel_desc;
+
+typedef struct hankel_plan_s* hankel_plan_t;
+typedef struct CUstream_st* hankel_stream_t; /* same type as cudaStream_t */
+
+/* Read-only facts about a plan (for logging and tests). */
+typedef struct hankel_plan_info {
+    int64_t count;            /* descriptors */
+    int64_t jobs;             /* kernel work units (a unit holds 1 or 2 tensors) */
+    int64_t launches;         /* kernel launches per hankel_txv() */
+    int64_t distinct_lengths; /* distinct FFT lengths L (bins) */
+    int64_t max_length;       /* largest L */
+    int64_t sum_length;       /* sum over descriptors of L */
+    int64_t workspace_bytes;  /* device workspace owned by the plan */
+    int64_t h_elems;          /* minimum h/x/y buffer sizes implied by the offsets */
+    int64_t x_elems;
+    int64_t y_elems;
+} hankel_plan_info;
+
+/*
+ * hankel_plan -- validate `count` descriptors and build a reusable plan.
+ * Section 3 (problem statement of the products and the embedding length).
+ *   out     receives the plan (set to NULL on failure).
+ *   descs   host array of `count` descriptors (copied; may be freed after).
+ *   dtype   element type of every buffer used with the plan.
+ *   flags   HANKEL_* flags above.
+ * Chooses per tensor the FFT length L >= d (a 2,3,5,7-smooth length chosen
+ * by a cost model, the same for every call), groups tensors into jobs and
+ * kernel launches, builds FP64-generated twiddle tables on the current device
+ * and allocates workspace.  Synchronous.
+ * Errors: EINVAL for m out of range, a non-positive size, negative offsets,
+ * a length beyond the supported maximum; ENOMEM; ECUDA.
+ */
+hankel_status hankel_plan(hankel_plan_t* out, const hankel_desc* descs, int64_t count,
+                          hankel_dtype dtype, uint32_t flags);
+
+/*
+ * hankel_txv -- y = H x_2 ... x_m and/or alpha = H x_1 ... x_m for every
+ * descriptor (Section 3, the fast procedures for y and alpha).
+ *   h, x   device buffers of generating vectors and mode vectors.
+ *   y      device buffer receiving each y at y_off (NULL: y not computed).
+ *   alpha  device array of `count` elements receiving alpha per descriptor
+ *          (NULL: not computed).  For real dtypes alpha is real.
+ * At least one of y and alpha must be non-NULL.  Real dtypes return real y
+ * (the imaginary part of the final transform is not an output).
+ * Errors: EINVAL (NULL plan, both outputs NULL, plan made with
+ * HANKEL_BLOCK), ECUDA (launch failure).
+ */
+hankel_status hankel_txv(hankel_plan_t plan, const void* h, const void* x, void* y, void* alpha,
+                         hankel_stream_t stream);
+
+/*
+ * hankel_txv_host -- hankel_txv on HOST buffers: copies h and x to plan-owned
+ * device staging buffers, computes, copies y / alpha back, all queued on
+ * `stream`; returns after the stream has finished (the host buffers are
+ * ready).  Pinned host memory makes the copies asynchronous DMA.  The first
+ * call allocates the staging buffers (they live until hankel_plan_destroy).
+ * Errors: as hankel_txv, plus ENOMEM.
+ */
+hankel_status hankel_txv_host(hankel_plan_t plan, const void* h, const void* x, void* y, void* alpha,
+                              hankel_stream_t stream);
+
+/*
+ * hankel_txv_block -- BHHB products (Section 3, the block procedures):
+ *   Y = vec^{-1}( H x_2 ... x_m ) = fft2(ifft2(H~) .* fft2(X~_2) ... )[0:n_1, 0:N_1],
+ *   alpha = <ifft2(H~), fft2(X~_1) .* ... .* fft2(X~_m)>.
+ * Buffers as hankel_txv, with column-major matrices (Section 3's vec).
+ * The plan must have been made with HANKEL_BLOCK.
+ */
+hankel_status hankel_txv_block(hankel_plan_t plan, const void* H, const void* X, void* Y, void* alpha,
+                               hankel_stream_t stream);
+
+/*
+ * hankel_txv_backward -- gradients of a real loss through y (not in the
+ * paper; the adjoints of the Section 3 products).  With z = x_2 * ... * x_m
+ * (linear convolution) and g = dLoss/dy:
+ *   grad_h[j]   = sum_i g_i conj(z[j - i]),                 j < d
+ *   grad_x_p    = conj(H x_1 conj(g) x_q ... x_q), mode p free (q != 1, p),
+ *   with HANKEL_SAME_X: grad_x = sum_p grad_x_p = (m-1) conj(H x_1 conj(g) x_3 x ... x_m x).
+ * For complex dtypes g and the gradients follow PyTorch's convention
+ * (dL/dRe + i dL/dIm), i.e. the adjoint of the map is applied.  BHHB plans use
+ * the 2D analogue.
+ *   grad_y  device buffer laid out like y.
+ *   grad_h  device buffer laid out like h (NULL: not computed).
+ *   grad_x  device buffer laid out like x (NULL: not computed).
+ * Gradients are WRITTEN, not accumulated; where several descriptors share one
+ * h or x region the contributions are summed into it.
+ * With HANKEL_STORE_SPECTRA the spectra saved by the last hankel_txv() on
+ * this plan are reused (they must come from the same h and x).
+ */
+hankel_status hankel_txv_backward(hankel_plan_t plan, const void* grad_y, const void* h, const void* x,
+                                  void* grad_h, void* grad_x, hankel_stream_t stream);
+
+/* hankel_plan_query -- copy the plan's facts into *info. */
+hankel_status hankel_plan_query(hankel_plan_t plan, hankel_plan_info* info);
+
+/* hankel_fft_length -- the FFT length the planner picks for generating
+ * length d (d >= 1), or -1 when d is beyond the supported maximum. */
+int64_t hankel_fft_length(int64_t d);
+
+/* hankel_plan_destroy -- free the plan and everything it owns (synchronises
+ * the device first).  NULL is ignored. */
+void hankel_plan_destroy(hankel_plan_t plan);
+
+/* hankel_last_error -- message for the calling thread's last failed call
+ * ("" if none).  The pointer stays valid until the thread's next call. */
+const char* hankel_last_error(void);
+
+/* hankel_version -- library version string. */
+const char* hankel_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HANKEL_H */

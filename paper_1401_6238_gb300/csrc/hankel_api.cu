@@ -1,0 +1,524 @@
+// hankel_api.cu -- the C ABI of include/hankel.h: planning (host), validation,
+// dispatch of the kernels, status codes.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "general.h"
+#include "hankel.h"
+#include "jobs.h"
+#include "launch.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+hankel_status fail(hankel_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+hankel_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(e == cudaErrorMemoryAllocation ? HANKEL_ENOMEM : HANKEL_ECUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+bool is_double(hankel_dtype d) { return d == HANKEL_R64 || d == HANKEL_C128; }
+bool is_complex(hankel_dtype d) { return d == HANKEL_C64 || d == HANKEL_C128; }
+size_t real_size(hankel_dtype d) { return is_double(d) ? 8 : 4; }
+size_t elem_size(hankel_dtype d) { return real_size(d) * (is_complex(d) ? 2 : 1); }
+
+// ------------------------------------------------------------ FFT lengths
+// Radix set of the kernels and a per-point cost model of one Stockham pass
+// (shared-memory round trip + butterfly arithmetic, FP32 operations / point).
+constexpr int kMaxL = 16384;
+constexpr double kPassCost = 10.0;
+double radix_cost(int r) {
+    switch (r) {
+        case 2: return 5.0;
+        case 3: return 9.3;
+        case 4: return 8.5;
+        case 5: return 12.8;
+        case 7: return 16.5;
+        case 8: return 12.75;
+        case 16: return 17.4;
+    }
+    return 1e9;
+}
+
+struct LenInfo {
+    int L;
+    std::vector<int> radix;
+    double cost;
+};
+
+// Best pass sequence for L = 2^a 3^b 5^c 7^e: the power of two split into
+// parts 16/8/4/2 minimising the model, odd primes one pass each.
+bool factor(int L, std::vector<int>& out, double& cost) {
+    int a = 0, v = L;
+    while (v % 2 == 0) { v /= 2; ++a; }
+    std::vector<int> odd;
+    for (int p : {3, 5, 7})
+        while (v % p == 0) { v /= p; odd.push_back(p); }
+    if (v != 1) return false;
+    // split a into parts of size 4,3,2,1 (log2 of 16,8,4,2)
+    double best = 1e18;
+    std::vector<int> bestp;
+    for (int n4 = 0; n4 * 4 <= a; ++n4)
+        for (int n3 = 0; n4 * 4 + n3 * 3 <= a; ++n3)
+            for (int n2 = 0; n4 * 4 + n3 * 3 + n2 * 2 <= a; ++n2) {
+                int n1 = a - n4 * 4 - n3 * 3 - n2 * 2;
+                std::vector<int> p;
+                p.insert(p.end(), n4, 16);
+                p.insert(p.end(), n3, 8);
+                p.insert(p.end(), n2, 4);
+                p.insert(p.end(), n1, 2);
+                double c = 0;
+                for (int r : p) c += kPassCost + radix_cost(r);
+                if (c < best || (c == best && p.size() < bestp.size())) { best = c; bestp = p; }
+            }
+    out = bestp;
+    out.insert(out.end(), odd.begin(), odd.end());
+    std::sort(out.begin(), out.end(), [](int x, int y) { return x > y; });
+    cost = 0;
+    for (int r : out) cost += kPassCost + radix_cost(r);
+    cost *= L;
+    return !out.empty() && out.size() <= 8;
+}
+
+struct LengthTable {
+    std::vector<LenInfo> cands;  // sorted by L
+    std::vector<int> best_from;  // index of the cheapest candidate at or after i
+    LengthTable() {
+        for (int L = 2; L <= kMaxL; ++L) {
+            LenInfo li;
+            li.L = L;
+            if (factor(L, li.radix, li.cost)) cands.push_back(li);
+        }
+        best_from.resize(cands.size());
+        int b = (int)cands.size() - 1;
+        for (int i = (int)cands.size() - 1; i >= 0; --i) {
+            if (cands[i].cost <= cands[b].cost) b = i;
+            best_from[i] = b;
+        }
+    }
+    const LenInfo* find(int L) const {
+        auto it = std::lower_bound(cands.begin(), cands.end(), L,
+                                   [](const LenInfo& li, int v) { return li.L < v; });
+        return (it != cands.end() && it->L == L) ? &*it : nullptr;
+    }
+    const LenInfo* pick(int64_t d) const {
+        if (d < 1 || d > kMaxL) return nullptr;
+        auto it = std::lower_bound(cands.begin(), cands.end(), (int)d,
+                                   [](const LenInfo& li, int v) { return li.L < v; });
+        if (it == cands.end()) return nullptr;
+        return &cands[best_from[it - cands.begin()]];
+    }
+};
+
+const LengthTable& lengths() {
+    static LengthTable t;
+    return t;
+}
+
+int pow2ceil(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+}  // namespace
+
+struct hankel_plan_s {
+    int device = 0;
+    hankel_dtype dtype = HANKEL_R32;
+    uint32_t flags = 0;
+    std::vector<hankel_desc> descs;
+    std::vector<int> Lof;
+    bool real_path = false;
+    // fused real path
+    std::vector<hk::RealJob> fwd_jobs, bwd_jobs;
+    std::vector<hk::RealLaunch> fwd_launches, bwd_launches;
+    hk::RealJob* d_fwd = nullptr;
+    hk::RealJob* d_bwd = nullptr;
+    // general path (complex data, distinct vectors, BHHB)
+    hk::GeneralPlan* gen = nullptr;
+    // twiddle tables and workspace
+    std::map<int, int> tw_off;
+    void* d_tw = nullptr;
+    void* d_ws = nullptr;
+    size_t ws_bytes = 0;
+    int64_t sum_L = 0, max_L = 0;
+    int64_t h_elems = 0, x_elems = 0, y_elems = 0;
+    // staging buffers of hankel_txv_host
+    void *s_h = nullptr, *s_x = nullptr, *s_y = nullptr, *s_a = nullptr;
+};
+
+namespace {
+
+void free_plan(hankel_plan_s* p) {
+    if (!p) return;
+    cudaFree(p->d_fwd);
+    cudaFree(p->d_bwd);
+    cudaFree(p->d_tw);
+    cudaFree(p->d_ws);
+    cudaFree(p->s_h);
+    cudaFree(p->s_x);
+    cudaFree(p->s_y);
+    cudaFree(p->s_a);
+    if (p->gen) hk::general_destroy(p->gen);
+    delete p;
+}
+
+hankel_status validate(const hankel_desc& d, int64_t i, uint32_t flags, int64_t& gen_len) {
+    if (d.m < 2 || d.m > HANKEL_MAX_ORDER)
+        return fail(HANKEL_EINVAL, "descriptor %lld: order m=%d outside [2, %d]", (long long)i, d.m,
+                    HANKEL_MAX_ORDER);
+    int64_t s = 0;
+    for (int p = 0; p < d.m; ++p) {
+        if (d.n[p] < 1) return fail(HANKEL_EINVAL, "descriptor %lld: n[%d]=%d must be >= 1", (long long)i, p, d.n[p]);
+        if ((flags & HANKEL_BLOCK) && d.N[p] < 1)
+            return fail(HANKEL_EINVAL, "descriptor %lld: N[%d]=%d must be >= 1", (long long)i, p, d.N[p]);
+        s += d.n[p];
+    }
+    gen_len = s - d.m + 1;
+    if (d.h_off < 0 || d.y_off < 0) return fail(HANKEL_EINVAL, "descriptor %lld: negative offset", (long long)i);
+    const int nx = (flags & HANKEL_SAME_X) ? 1 : d.m;
+    for (int p = 0; p < nx; ++p)
+        if (d.x_off[p] < 0) return fail(HANKEL_EINVAL, "descriptor %lld: negative x_off[%d]", (long long)i, p);
+    return HANKEL_OK;
+}
+
+hankel_status upload_twiddles(hankel_plan_s* p, const std::vector<int>& Ls) {
+    int64_t total = 0;
+    for (int L : Ls) {
+        if (p->tw_off.count(L)) continue;
+        p->tw_off[L] = (int)total;
+        total += L;
+    }
+    const size_t cs = 2 * real_size(p->dtype);
+    cudaError_t e = cudaMalloc(&p->d_tw, std::max<int64_t>(total, 1) * cs);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(twiddles)");
+    for (auto& kv : p->tw_off) {
+        e = hk::launch_twiddles(is_double(p->dtype), (char*)p->d_tw + (size_t)kv.second * cs, kv.first, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "twiddle kernel");
+    }
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "twiddle generation");
+    return HANKEL_OK;
+}
+
+// Threads per block for a transform of length L: about one radix-16
+// butterfly per thread and pass, between one warp and 512 threads.
+int nthr_of(int L) { return std::max(32, std::min(512, pow2ceil((L + 15) / 16))); }
+
+// Largest L whose `buffers` ping-pong arrays fit in one block's shared memory.
+constexpr size_t kSmemLimit = 227 * 1024;
+int max_len_for(int buffers, size_t csize) {
+    int L = 2;
+    while (L + 1 <= kMaxL &&
+           hk::RED_BYTES + (size_t)buffers * hk::smem_elems_host(L + 1) * csize <= kSmemLimit)
+        ++L;
+    return L;
+}
+
+// Group jobs into launches of one block size each, largest transforms first.
+void make_launches(std::vector<hk::RealJob>& jobs, std::vector<hk::RealLaunch>& launches, bool one_per_launch,
+                   int single_buffers) {
+    std::stable_sort(jobs.begin(), jobs.end(), [](const hk::RealJob& a, const hk::RealJob& b) {
+        return a.P.L > b.P.L;
+    });
+    launches.clear();
+    for (size_t i = 0; i < jobs.size();) {
+        const int L0 = jobs[i].P.L;
+        hk::RealLaunch lc;
+        lc.first = (int)i;
+        lc.nthr = nthr_of(L0);
+        lc.emax = 0;
+        lc.Lmax = L0;
+        lc.arrays = jobs[i].single ? single_buffers : 3;
+        size_t j = i + 1;
+        if (!one_per_launch)
+            while (j < jobs.size() && nthr_of(jobs[j].P.L) == lc.nthr) {
+                if (!jobs[j].single) lc.arrays = 3;
+                ++j;
+            }
+        lc.count = (int)(j - i);
+        launches.push_back(lc);
+        i = j;
+    }
+}
+
+hk::FftPlan fft_plan_of(const hankel_plan_s* p, int L) {
+    const LenInfo* li = lengths().find(L);
+    hk::FftPlan P;
+    P.L = L;
+    P.npass = (int)li->radix.size();
+    P.tw_off = p->tw_off.at(L);
+    for (int i = 0; i < 8; ++i) P.radix[i] = i < P.npass ? (uint8_t)li->radix[i] : 0;
+    return P;
+}
+
+hankel_status build_real_path(hankel_plan_s* p) {
+    const int64_t count = (int64_t)p->descs.size();
+    const bool dbl = is_double(p->dtype);
+    const size_t cs = 2 * real_size(p->dtype);
+    const int max_pair_L = max_len_for(3, cs);
+    const int max_single_L = max_len_for(2, cs);
+    for (int64_t i = 0; i < count; ++i)
+        if (p->Lof[i] > max_single_L)
+            return fail(HANKEL_EUNSUPPORTED, "descriptor %lld: FFT length %d exceeds the shared-memory limit %d of "
+                        "this build for this dtype", (long long)i, p->Lof[i], max_single_L);
+    const bool singles = (p->flags & (HANKEL_STORE_SPECTRA | HANKEL_ONE_PER_LAUNCH)) != 0;
+    std::vector<int64_t> ws_off(count);
+    int64_t ws = 0;
+    for (int64_t i = 0; i < count; ++i) {
+        ws_off[i] = ws;
+        ws += p->Lof[i];
+    }
+    auto fill = [&](hk::RealJob& J, int64_t i, bool B) {
+        const hankel_desc& d = p->descs[i];
+        const int dl = (int)(d.n[0] * (int64_t)d.m - d.m + 1);
+        if (!B) {
+            J.mA = d.m; J.nA = d.n[0]; J.dA = dl; J.iA = (int)i;
+            J.hA = d.h_off; J.xA = d.x_off[0]; J.yA = d.y_off; J.wsA = ws_off[i];
+        } else {
+            J.mB = d.m; J.nB = d.n[0]; J.dB = dl; J.iB = (int)i;
+            J.hB = d.h_off; J.xB = d.x_off[0]; J.yB = d.y_off; J.wsB = ws_off[i];
+        }
+    };
+    std::vector<int64_t> order(count);
+    for (int64_t i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return p->Lof[a] < p->Lof[b]; });
+    p->fwd_jobs.clear();
+    p->bwd_jobs.clear();
+    for (size_t k = 0; k < order.size();) {
+        hk::RealJob J;
+        std::memset(&J, 0, sizeof(J));
+        const int64_t a = order[k];
+        const int L = p->Lof[a];
+        J.P = fft_plan_of(p, L);
+        fill(J, a, false);
+        J.iB = -1;
+        if (!singles && L <= max_pair_L && k + 1 < order.size() && p->Lof[order[k + 1]] == L) {
+            fill(J, order[k + 1], true);
+            J.single = 0;
+            k += 2;
+        } else {
+            J.single = 1;
+            k += 1;
+        }
+        p->fwd_jobs.push_back(J);
+    }
+    for (int64_t i = 0; i < count; ++i) {
+        hk::RealJob J;
+        std::memset(&J, 0, sizeof(J));
+        J.P = fft_plan_of(p, p->Lof[i]);
+        fill(J, i, false);
+        J.single = 1;
+        J.iB = -1;
+        p->bwd_jobs.push_back(J);
+    }
+    const bool opl = (p->flags & HANKEL_ONE_PER_LAUNCH) != 0;
+    make_launches(p->fwd_jobs, p->fwd_launches, opl, 2);
+    make_launches(p->bwd_jobs, p->bwd_launches, opl, 2);
+    for (auto* v : {&p->fwd_launches, &p->bwd_launches})
+        for (auto& lc : *v)
+            if (hk::real_launch_smem(dbl, lc) > kSmemLimit)
+                return fail(HANKEL_EUNSUPPORTED, "FFT length %d needs more shared memory than a block has", lc.Lmax);
+    cudaError_t e;
+    const size_t jb = sizeof(hk::RealJob);
+    e = cudaMalloc(&p->d_fwd, std::max<size_t>(p->fwd_jobs.size(), 1) * jb);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(jobs)");
+    e = cudaMalloc(&p->d_bwd, std::max<size_t>(p->bwd_jobs.size(), 1) * jb);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(jobs)");
+    e = cudaMemcpy(p->d_fwd, p->fwd_jobs.data(), p->fwd_jobs.size() * jb, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(jobs)");
+    e = cudaMemcpy(p->d_bwd, p->bwd_jobs.data(), p->bwd_jobs.size() * jb, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(jobs)");
+    p->ws_bytes = (size_t)std::max<int64_t>(ws, 1) * 2 * real_size(p->dtype);
+    e = cudaMalloc(&p->d_ws, p->ws_bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(workspace)");
+    return HANKEL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hankel_status hankel_plan(hankel_plan_t* out, const hankel_desc* descs, int64_t count, hankel_dtype dtype,
+                          uint32_t flags) {
+    if (out == nullptr) return fail(HANKEL_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (descs == nullptr || count < 1) return fail(HANKEL_EINVAL, "need at least one descriptor");
+    if (dtype < HANKEL_R32 || dtype > HANKEL_C128) return fail(HANKEL_EINVAL, "unknown dtype %d", (int)dtype);
+    if (flags & ~(uint32_t)0x1F) return fail(HANKEL_EINVAL, "unknown flag bits 0x%x", flags);
+    auto* p = new (std::nothrow) hankel_plan_s;
+    if (!p) return fail(HANKEL_ENOMEM, "host allocation failed");
+    p->dtype = dtype;
+    p->flags = flags;
+    cudaGetDevice(&p->device);
+    p->descs.assign(descs, descs + count);
+    const bool block = (flags & HANKEL_BLOCK) != 0;
+    const int64_t maxL = kMaxL;
+    std::vector<int> Ls;
+    for (int64_t i = 0; i < count; ++i) {
+        int64_t d;
+        hankel_status s = validate(descs[i], i, flags, d);
+        if (s != HANKEL_OK) { free_plan(p); return s; }
+        const hankel_desc& D = descs[i];
+        const int nx = (flags & HANKEL_SAME_X) ? 1 : D.m;
+        if (!block) {
+            const LenInfo* li = lengths().pick(d);
+            if (!li || li->L > maxL) {
+                free_plan(p);
+                return fail(HANKEL_EUNSUPPORTED, "descriptor %lld: generating length d=%lld exceeds the maximum "
+                            "FFT length %lld of this build", (long long)i, (long long)d, (long long)maxL);
+            }
+            p->Lof.push_back(li->L);
+            Ls.push_back(li->L);
+            p->sum_L += li->L;
+            p->max_L = std::max<int64_t>(p->max_L, li->L);
+            p->h_elems = std::max<int64_t>(p->h_elems, D.h_off + d);
+            for (int q = 0; q < nx; ++q) p->x_elems = std::max<int64_t>(p->x_elems, D.x_off[q] + D.n[q]);
+            p->y_elems = std::max<int64_t>(p->y_elems, D.y_off + D.n[0]);
+        }
+    }
+    bool square = true;
+    if (!block)
+        for (auto& D : p->descs)
+            for (int q = 1; q < D.m; ++q) square = square && D.n[q] == D.n[0];
+    p->real_path = !block && !is_complex(dtype) && (flags & HANKEL_SAME_X) && square;
+    hankel_status s = HANKEL_OK;
+    if (p->real_path) {
+        s = upload_twiddles(p, Ls);
+        if (s == HANKEL_OK) s = build_real_path(p);
+    } else {
+        s = hk::general_create(&p->gen, p->descs, dtype, flags, &p->h_elems, &p->x_elems, &p->y_elems,
+                               &p->sum_L, &p->max_L, g_err);
+    }
+    if (s != HANKEL_OK) { free_plan(p); return s; }
+    *out = p;
+    return HANKEL_OK;
+}
+
+hankel_status hankel_txv(hankel_plan_t p, const void* h, const void* x, void* y, void* alpha, hankel_stream_t stream) {
+    if (!p) return fail(HANKEL_EINVAL, "plan is NULL");
+    if (p->flags & HANKEL_BLOCK) return fail(HANKEL_EINVAL, "plan was made for BHHB tensors: use hankel_txv_block");
+    if (!h || !x) return fail(HANKEL_EINVAL, "h and x must be device pointers");
+    if (!y && !alpha) return fail(HANKEL_EINVAL, "nothing to compute: y and alpha are both NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!p->real_path) return hk::general_forward(p->gen, h, x, y, alpha, st, g_err);
+    const bool dbl = is_double(p->dtype);
+    for (auto& lc : p->fwd_launches) {
+        cudaError_t e = hk::launch_real_forward(dbl, lc, p->d_fwd, h, x, y, alpha, p->d_tw, p->d_ws, (int)p->flags, st);
+        if (e != cudaSuccess) return cuda_fail(e, "forward kernel launch");
+    }
+    return HANKEL_OK;
+}
+
+hankel_status hankel_txv_host(hankel_plan_t p, const void* h, const void* x, void* y, void* alpha,
+                              hankel_stream_t stream) {
+    if (!p) return fail(HANKEL_EINVAL, "plan is NULL");
+    if (!h || !x) return fail(HANKEL_EINVAL, "h and x must be host pointers");
+    if (!y && !alpha) return fail(HANKEL_EINVAL, "nothing to compute: y and alpha are both NULL");
+    const size_t es = elem_size(p->dtype);
+    const size_t hb = (size_t)std::max<int64_t>(p->h_elems, 1) * es;
+    const size_t xb = (size_t)std::max<int64_t>(p->x_elems, 1) * es;
+    const size_t yb = (size_t)std::max<int64_t>(p->y_elems, 1) * es;
+    const size_t ab = (size_t)p->descs.size() * es;
+    cudaError_t e;
+    if (!p->s_h) {
+        if ((e = cudaMalloc(&p->s_h, hb)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(staging)");
+        if ((e = cudaMalloc(&p->s_x, xb)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(staging)");
+        if ((e = cudaMalloc(&p->s_y, yb)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(staging)");
+        if ((e = cudaMalloc(&p->s_a, ab)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(staging)");
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((e = cudaMemcpyAsync(p->s_h, h, hb, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_fail(e, "H2D");
+    if ((e = cudaMemcpyAsync(p->s_x, x, xb, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_fail(e, "H2D");
+    hankel_status s = (p->flags & HANKEL_BLOCK)
+                          ? hankel_txv_block(p, p->s_h, p->s_x, y ? p->s_y : nullptr, alpha ? p->s_a : nullptr, stream)
+                          : hankel_txv(p, p->s_h, p->s_x, y ? p->s_y : nullptr, alpha ? p->s_a : nullptr, stream);
+    if (s != HANKEL_OK) return s;
+    if (y && (e = cudaMemcpyAsync(y, p->s_y, yb, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(e, "D2H");
+    if (alpha && (e = cudaMemcpyAsync(alpha, p->s_a, ab, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(e, "D2H");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    return HANKEL_OK;
+}
+
+hankel_status hankel_txv_block(hankel_plan_t p, const void* H, const void* X, void* Y, void* alpha,
+                               hankel_stream_t stream) {
+    if (!p) return fail(HANKEL_EINVAL, "plan is NULL");
+    if (!(p->flags & HANKEL_BLOCK)) return fail(HANKEL_EINVAL, "plan was not made with HANKEL_BLOCK");
+    if (!H || !X) return fail(HANKEL_EINVAL, "H and X must be device pointers");
+    if (!Y && !alpha) return fail(HANKEL_EINVAL, "nothing to compute: Y and alpha are both NULL");
+    return hk::general_forward(p->gen, H, X, Y, alpha, (cudaStream_t)stream, g_err);
+}
+
+hankel_status hankel_txv_backward(hankel_plan_t p, const void* grad_y, const void* h, const void* x, void* grad_h,
+                                  void* grad_x, hankel_stream_t stream) {
+    if (!p) return fail(HANKEL_EINVAL, "plan is NULL");
+    if (!grad_y || !h || !x) return fail(HANKEL_EINVAL, "grad_y, h and x must be device pointers");
+    if (!grad_h && !grad_x) return fail(HANKEL_EINVAL, "nothing to compute: grad_h and grad_x are both NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!p->real_path) return hk::general_backward(p->gen, grad_y, h, x, grad_h, grad_x, st, g_err);
+    const bool dbl = is_double(p->dtype);
+    const int stored = (p->flags & HANKEL_STORE_SPECTRA) ? 1 : 0;
+    for (auto& lc : p->bwd_launches) {
+        cudaError_t e = hk::launch_real_backward(dbl, lc, p->d_bwd, grad_y, h, x, grad_h, grad_x, p->d_tw, p->d_ws,
+                                                 (int)p->flags, stored, st);
+        if (e != cudaSuccess) return cuda_fail(e, "backward kernel launch");
+    }
+    return HANKEL_OK;
+}
+
+hankel_status hankel_plan_query(hankel_plan_t p, hankel_plan_info* info) {
+    if (!p || !info) return fail(HANKEL_EINVAL, "NULL argument");
+    std::memset(info, 0, sizeof(*info));
+    info->count = (int64_t)p->descs.size();
+    info->sum_length = p->sum_L;
+    info->max_length = p->max_L;
+    info->h_elems = p->h_elems;
+    info->x_elems = p->x_elems;
+    info->y_elems = p->y_elems;
+    if (p->real_path) {
+        info->jobs = (int64_t)p->fwd_jobs.size();
+        info->launches = (int64_t)p->fwd_launches.size();
+        info->distinct_lengths = (int64_t)p->tw_off.size();
+        info->workspace_bytes = (int64_t)p->ws_bytes;
+    } else {
+        hk::general_info(p->gen, &info->jobs, &info->launches, &info->distinct_lengths, &info->workspace_bytes);
+    }
+    return HANKEL_OK;
+}
+
+int64_t hankel_fft_length(int64_t d) {
+    const LenInfo* li = lengths().pick(d);
+    return li ? li->L : -1;
+}
+
+void hankel_plan_destroy(hankel_plan_t p) {
+    if (!p) return;
+    cudaDeviceSynchronize();
+    free_plan(p);
+}
+
+const char* hankel_last_error(void) { return g_err.c_str(); }
+
+const char* hankel_version(void) { return "hankel-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,36 @@
+// jobs.h -- work descriptors shared by the host planner and the kernels.
+#pragma once
+
+#include <stdint.h>
+
+#include "hankel.h"
+
+namespace hk {
+
+// Plan of one length-L forward transform: L = radix[0] * ... * radix[npass-1],
+// twiddles exp(-2 pi i j / L), j < L, at tw_off in the plan's twiddle array.
+struct FftPlan {
+    int32_t L, npass, tw_off;
+    uint8_t radix[8];
+};
+
+// Real square tensors with one vector per tensor (y = H x^{m-1}).  A job is
+// either a pair (A, B) of tensors with the same L -- two real problems share
+// every complex transform -- or a single tensor, whose h and x share one
+// transform as h + i x.
+struct RealJob {
+    FftPlan P;
+    int32_t single;
+    int32_t mA, nA, dA, iA;
+    int32_t mB, nB, dB, iB;
+    int64_t hA, xA, yA, hB, xB, yB;
+    int64_t wsA, wsB;  // element offsets of each tensor's spectrum in the workspace
+};
+
+// Launch of one group of jobs that share a block size.
+struct RealLaunch {
+    int32_t first, count;  // range in the job table
+    int32_t nthr, emax, Lmax, arrays;
+};
+
+}  // namespace hk

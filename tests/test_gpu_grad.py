@@ -65,13 +65,14 @@ def test_autograd_matches_finite_differences_fp64(dev):
     plan = hk.Plan(hk.batch_descs(b), hk.R64, hk.SAME_X)
     H = torch.tensor(b.h, device=dev, requires_grad=True)
     X = torch.tensor(b.x, device=dev, requires_grad=True)
-    t = torch.tensor(np.random.default_rng(2).standard_normal(b.y_len), device=dev)
+    ny = plan.info["y_elems"]
+    t = torch.tensor(np.random.default_rng(2).standard_normal(ny), device=dev)
     y = hk.hankel_txv_autograd(H, X, plan)
     loss = ((y - t) ** 2).sum()
     loss.backward()
 
     def f(hv, xv):
-        y = torch.zeros(b.y_len, dtype=torch.float64, device=dev)
+        y = torch.zeros(ny, dtype=torch.float64, device=dev)
         plan.txv(hv, xv, y)
         return float(((y - t) ** 2).sum())
 

@@ -140,6 +140,22 @@ int pow2ceil(int v) {
 
 }  // namespace
 
+namespace hk {
+// The planner's pass sequence for FFT length L (tw_off left at 0); false if
+// L is not one of the planner's lengths.
+bool fft_factor(int L, FftPlan* P) {
+    const LenInfo* li = lengths().find(L);
+    if (li == nullptr) return false;
+    std::memset(P, 0, sizeof(*P));
+    P->L = L;
+    P->npass = (int)li->radix.size();
+    for (int i = 0; i < P->npass && i < 8; ++i) P->radix[i] = (uint8_t)li->radix[i];
+    return true;
+}
+// Record the message hankel_last_error() returns for this thread.
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace hk
+
 struct hankel_plan_s {
     int device = 0;
     hankel_dtype dtype = HANKEL_R32;
@@ -233,10 +249,12 @@ int max_len_for(int buffers, size_t csize) {
     return L;
 }
 
-// Group jobs into launches of one block size each, largest transforms first.
+// Group jobs into launches of one block size and one job kind each (pairs
+// need three shared buffers, singles two), largest transforms first.
 void make_launches(std::vector<hk::RealJob>& jobs, std::vector<hk::RealLaunch>& launches, bool one_per_launch,
                    int single_buffers) {
     std::stable_sort(jobs.begin(), jobs.end(), [](const hk::RealJob& a, const hk::RealJob& b) {
+        if (a.single != b.single) return a.single < b.single;
         return a.P.L > b.P.L;
     });
     launches.clear();
@@ -250,10 +268,7 @@ void make_launches(std::vector<hk::RealJob>& jobs, std::vector<hk::RealLaunch>& 
         lc.arrays = jobs[i].single ? single_buffers : 3;
         size_t j = i + 1;
         if (!one_per_launch)
-            while (j < jobs.size() && nthr_of(jobs[j].P.L) == lc.nthr) {
-                if (!jobs[j].single) lc.arrays = 3;
-                ++j;
-            }
+            while (j < jobs.size() && nthr_of(jobs[j].P.L) == lc.nthr && jobs[j].single == jobs[i].single) ++j;
         lc.count = (int)(j - i);
         launches.push_back(lc);
         i = j;

@@ -200,6 +200,43 @@ hankel_status hankel_txv_block(hankel_plan_t plan, const void* H, const void* X,
 hankel_status hankel_txv_backward(hankel_plan_t plan, const void* grad_y, const void* h, const void* x,
                                   void* grad_h, void* grad_x, hankel_stream_t stream);
 
+/*
+ * hankel_txv_backward_static -- the gradients hankel_txv_backward computes, for
+ * real square tensors with one vector per tensor (the HANKEL_SAME_X case:
+ * x_off[0] in every mode), WITHOUT allocating any device memory.  The paper
+ * has no counterpart to this call.
+ *
+ * Some callers cannot call cudaMalloc: a process whose device memory is
+ * already owned by another allocator (a framework's caching allocator that
+ * has reserved the GPU), a latency-critical loop that cannot pay for
+ * cudaMalloc/cudaFree (they synchronise the device), or a deployment whose
+ * device footprint must stay fixed after start-up.  This call needs no plan:
+ * it takes the descriptors directly (host array, as for hankel_plan), passes
+ * its job table as kernel arguments, and keeps its scratch -- the twiddle
+ * tables and one spectrum of L complex values per tensor -- in a single
+ * static device array of HANKEL_STATIC_SCRATCH_BYTES, which every GPU that
+ * loads the library holds until the process exits.
+ *   descs, count  as hankel_plan (copied during the call).
+ *   dtype         HANKEL_R32 or HANKEL_R64.
+ *   grad_y, h, x  device buffers laid out as for hankel_txv_backward.
+ *   grad_h/grad_x device outputs (either may be NULL), written, not accumulated.
+ * A batch whose scratch would exceed the array (the sum over tensors of
+ * L * 2 * sizeof(real), plus one twiddle table per distinct L, each rounded
+ * up to 256 bytes) is rejected with HANKEL_EINVAL and a message giving the
+ * bytes it needs; so are non-square tensors and FFT lengths beyond the
+ * shared-memory limit.  No cudaMalloc, cudaFree or allocating library call is
+ * made.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current: make that first call
+ * before any stream capture.  Every call shares the array and overwrites the
+ * parts it uses (nothing in it needs to start at zero), so calls that overlap
+ * on the GPU -- on two streams, or from two host threads -- race; the caller
+ * must serialise them.
+ */
+#define HANKEL_STATIC_SCRATCH_BYTES (16u << 20)
+hankel_status hankel_txv_backward_static(const hankel_desc* descs, int64_t count, hankel_dtype dtype,
+                                         const void* grad_y, const void* h, const void* x, void* grad_h,
+                                         void* grad_x, hankel_stream_t stream);
+
 /* hankel_plan_query -- copy the plan's facts into *info. */
 hankel_status hankel_plan_query(hankel_plan_t plan, hankel_plan_info* info);
 

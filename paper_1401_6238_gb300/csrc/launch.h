@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <string>
+
 #include "jobs.h"
 
 namespace hk {
@@ -20,5 +22,7 @@ cudaError_t launch_real_backward(bool dbl, const RealLaunch& lc, const RealJob* 
                                  cudaStream_t st);
 cudaError_t launch_twiddles(bool dbl, void* out, int L, cudaStream_t st);
 size_t real_launch_smem(bool dbl, const RealLaunch& lc);
+bool fft_factor(int L, FftPlan* P);
+void set_last_error(const std::string& msg);
 
 }  // namespace hk

@@ -58,6 +58,8 @@ _SIGS = {
     "hankel_txv_host": (ctypes.c_int, [ctypes.c_void_p] * 6),
     "hankel_txv_block": (ctypes.c_int, [ctypes.c_void_p] * 6),
     "hankel_txv_backward": (ctypes.c_int, [ctypes.c_void_p] * 7),
+    "hankel_txv_backward_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int] +
+                                   [ctypes.c_void_p] * 6),
     "hankel_plan_query": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(PlanInfo)]),
     "hankel_fft_length": (ctypes.c_int64, [ctypes.c_int64]),
     "hankel_plan_destroy": (None, [ctypes.c_void_p]),
@@ -134,6 +136,18 @@ def hankel_txv_block(plan, H, X, Y, alpha, stream=None):
 def hankel_txv_backward(plan, grad_y, h, x, grad_h, grad_x, stream=None):
     _check(load().hankel_txv_backward(plan, _ptr(grad_y), _ptr(h), _ptr(x), _ptr(grad_h), _ptr(grad_x),
                                       _stream(stream)))
+
+
+STATIC_SCRATCH_BYTES = 16 << 20
+
+
+def hankel_txv_backward_static(descs, dtype, grad_y, h, x, grad_h, grad_x, stream=None):
+    """Gradients of the real one-vector product without any device
+    allocation: the scratch is a static device array of STATIC_SCRATCH_BYTES
+    shared by every call (see include/hankel.h)."""
+    descs = np.ascontiguousarray(descs, dtype=DESC_DTYPE)
+    _check(load().hankel_txv_backward_static(descs.ctypes.data, descs.shape[0], int(dtype), _ptr(grad_y), _ptr(h),
+                                             _ptr(x), _ptr(grad_h), _ptr(grad_x), _stream(stream)))
 
 
 def hankel_plan_query(plan):

@@ -179,6 +179,9 @@ struct hankel_plan_s {
     int64_t h_elems = 0, x_elems = 0, y_elems = 0;
     // staging buffers of hankel_txv_host
     void *s_h = nullptr, *s_x = nullptr, *s_y = nullptr, *s_a = nullptr;
+    // streams the independent launches of one call fork onto, and events
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> events;  // [0] fork, [1 + i] join of streams[i]
 };
 
 namespace {
@@ -193,6 +196,8 @@ void free_plan(hankel_plan_s* p) {
     cudaFree(p->s_x);
     cudaFree(p->s_y);
     cudaFree(p->s_a);
+    for (auto st : p->streams) cudaStreamDestroy(st);
+    for (auto ev : p->events) cudaEventDestroy(ev);
     if (p->gen) hk::general_destroy(p->gen);
     delete p;
 }
@@ -216,18 +221,24 @@ hankel_status validate(const hankel_desc& d, int64_t i, uint32_t flags, int64_t&
     return HANKEL_OK;
 }
 
+// Per-pass twiddle tables (fft_stage.cuh layout) of every distinct length.
 hankel_status upload_twiddles(hankel_plan_s* p, const std::vector<int>& Ls) {
     int64_t total = 0;
+    std::vector<hk::FftPlan> plans;
     for (int L : Ls) {
         if (p->tw_off.count(L)) continue;
+        hk::FftPlan P;
+        hk::fft_factor(L, &P);
         p->tw_off[L] = (int)total;
-        total += L;
+        P.tw_off = (int)total;
+        plans.push_back(P);
+        total += std::max(1, hk::stage_twiddle_count(P));
     }
     const size_t cs = 2 * real_size(p->dtype);
     cudaError_t e = cudaMalloc(&p->d_tw, std::max<int64_t>(total, 1) * cs);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(twiddles)");
-    for (auto& kv : p->tw_off) {
-        e = hk::launch_twiddles(is_double(p->dtype), (char*)p->d_tw + (size_t)kv.second * cs, kv.first, 0);
+    for (const auto& P : plans) {
+        e = hk::launch_stage_twiddles(is_double(p->dtype), (char*)p->d_tw + (size_t)P.tw_off * cs, P, 0);
         if (e != cudaSuccess) return cuda_fail(e, "twiddle kernel");
     }
     e = cudaDeviceSynchronize();
@@ -244,7 +255,8 @@ constexpr size_t kSmemLimit = 227 * 1024;
 int max_len_for(int buffers, size_t csize) {
     int L = 2;
     while (L + 1 <= kMaxL &&
-           hk::RED_BYTES + (size_t)buffers * hk::smem_elems_host(L + 1) * csize <= kSmemLimit)
+           hk::RED_BYTES + ((size_t)hk::TW_SMEM_HOST + (size_t)buffers * hk::smem_elems_host(L + 1)) * csize <=
+               kSmemLimit)
         ++L;
     return L;
 }
@@ -330,6 +342,11 @@ hankel_status build_real_path(hankel_plan_s* p) {
             fill(J, order[k + 1], true);
             J.single = 0;
             k += 2;
+        } else if (!singles && L <= max_pair_L) {
+            // a leftover tensor runs as a pair with an empty partner, so that
+            // it shares the pair launches instead of needing its own
+            J.single = 0;
+            k += 1;
         } else {
             J.single = 1;
             k += 1;
@@ -362,9 +379,50 @@ hankel_status build_real_path(hankel_plan_s* p) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(jobs)");
     e = cudaMemcpy(p->d_bwd, p->bwd_jobs.data(), p->bwd_jobs.size() * jb, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(jobs)");
+    const size_t nstreams = opl ? 0 : std::min<size_t>(8, std::max(p->fwd_launches.size(), p->bwd_launches.size()));
+    if (nstreams > 1) {
+        for (size_t i = 0; i < nstreams; ++i) {
+            cudaStream_t st;
+            e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+            p->streams.push_back(st);
+        }
+        for (size_t i = 0; i <= nstreams; ++i) {
+            cudaEvent_t ev;
+            e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+            p->events.push_back(ev);
+        }
+    }
     p->ws_bytes = (size_t)std::max<int64_t>(ws, 1) * 2 * real_size(p->dtype);
     e = cudaMalloc(&p->d_ws, p->ws_bytes);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(workspace)");
+    return HANKEL_OK;
+}
+
+// Queue independent launches: with the plan's streams, fork from `st`, run
+// launch i on stream i mod n, and join back into `st` (graph-capturable);
+// without them, run them in order on `st`.
+template <class F>
+hankel_status run_forked(hankel_plan_s* p, const std::vector<hk::RealLaunch>& launches, cudaStream_t st, F launch) {
+    cudaError_t e;
+    if (p->streams.empty() || launches.size() < 2) {
+        for (auto& lc : launches)
+            if ((e = launch(lc, st)) != cudaSuccess) return cuda_fail(e, "kernel launch");
+        return HANKEL_OK;
+    }
+    const size_t n = std::min(p->streams.size(), launches.size());
+    if ((e = cudaEventRecord(p->events[0], st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    for (size_t i = 0; i < n; ++i)
+        if ((e = cudaStreamWaitEvent(p->streams[i], p->events[0], 0)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamWaitEvent");
+    for (size_t i = 0; i < launches.size(); ++i)
+        if ((e = launch(launches[i], p->streams[i % n])) != cudaSuccess) return cuda_fail(e, "kernel launch");
+    for (size_t i = 0; i < n; ++i) {
+        if ((e = cudaEventRecord(p->events[1 + i], p->streams[i])) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+        if ((e = cudaStreamWaitEvent(st, p->events[1 + i], 0)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamWaitEvent");
+    }
     return HANKEL_OK;
 }
 
@@ -436,11 +494,9 @@ hankel_status hankel_txv(hankel_plan_t p, const void* h, const void* x, void* y,
     cudaStream_t st = (cudaStream_t)stream;
     if (!p->real_path) return hk::general_forward(p->gen, h, x, y, alpha, st, g_err);
     const bool dbl = is_double(p->dtype);
-    for (auto& lc : p->fwd_launches) {
-        cudaError_t e = hk::launch_real_forward(dbl, lc, p->d_fwd, h, x, y, alpha, p->d_tw, p->d_ws, (int)p->flags, st);
-        if (e != cudaSuccess) return cuda_fail(e, "forward kernel launch");
-    }
-    return HANKEL_OK;
+    return run_forked(p, p->fwd_launches, st, [&](const hk::RealLaunch& lc, cudaStream_t s) {
+        return hk::launch_real_forward(dbl, lc, p->d_fwd, h, x, y, alpha, p->d_tw, p->d_ws, (int)p->flags, s);
+    });
 }
 
 hankel_status hankel_txv_host(hankel_plan_t p, const void* h, const void* x, void* y, void* alpha,
@@ -493,12 +549,10 @@ hankel_status hankel_txv_backward(hankel_plan_t p, const void* grad_y, const voi
     if (!p->real_path) return hk::general_backward(p->gen, grad_y, h, x, grad_h, grad_x, st, g_err);
     const bool dbl = is_double(p->dtype);
     const int stored = (p->flags & HANKEL_STORE_SPECTRA) ? 1 : 0;
-    for (auto& lc : p->bwd_launches) {
-        cudaError_t e = hk::launch_real_backward(dbl, lc, p->d_bwd, grad_y, h, x, grad_h, grad_x, p->d_tw, p->d_ws,
-                                                 (int)p->flags, stored, st);
-        if (e != cudaSuccess) return cuda_fail(e, "backward kernel launch");
-    }
-    return HANKEL_OK;
+    return run_forked(p, p->bwd_launches, st, [&](const hk::RealLaunch& lc, cudaStream_t s) {
+        return hk::launch_real_backward(dbl, lc, p->d_bwd, grad_y, h, x, grad_h, grad_x, p->d_tw, p->d_ws,
+                                        (int)p->flags, stored, s);
+    });
 }
 
 hankel_status hankel_plan_query(hankel_plan_t p, hankel_plan_info* info) {

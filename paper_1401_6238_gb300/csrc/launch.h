@@ -14,6 +14,8 @@ namespace hk {
 constexpr int RED_BYTES = 512;
 // shared-memory elements of one padded length-L buffer (one pad slot per 16)
 constexpr size_t smem_elems_host(int L) { return (size_t)L + (size_t)(L >> 4) + 1; }
+// shared-memory slots of the real-path kernels' twiddle table (L <= 16384)
+constexpr int TW_SMEM_HOST = (16384 + 63) / 64 + 64;
 
 cudaError_t launch_real_forward(bool dbl, const RealLaunch& lc, const RealJob* jobs, const void* h, const void* x,
                                 void* y, void* alpha, const void* tw, void* ws, int flags, cudaStream_t st);
@@ -21,6 +23,9 @@ cudaError_t launch_real_backward(bool dbl, const RealLaunch& lc, const RealJob* 
                                  const void* x, void* gh, void* gx, const void* tw, void* ws, int flags, int stored,
                                  cudaStream_t st);
 cudaError_t launch_twiddles(bool dbl, void* out, int L, cudaStream_t st);
+// per-pass twiddle layout of fft_stage.cuh (real-data kernels)
+cudaError_t launch_stage_twiddles(bool dbl, void* out, const FftPlan& P, cudaStream_t st);
+int stage_twiddle_count(const FftPlan& P);
 size_t real_launch_smem(bool dbl, const RealLaunch& lc);
 bool fft_factor(int L, FftPlan* P);
 void set_last_error(const std::string& msg);

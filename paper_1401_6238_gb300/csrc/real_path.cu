@@ -19,10 +19,13 @@
 // reversed) and grad_x (imaginary part).
 #include <cuda_runtime.h>
 
-#include "fft_core.cuh"
+#include "fft_stage.cuh"
 #include "launch.h"
 
 namespace hk {
+
+// shared-memory slots reserved for the twiddle table (largest L = 16384)
+constexpr int TW_SMEM = tw_table_elems(16384);
 
 template <typename T>
 struct PairLoad {
@@ -99,43 +102,6 @@ __device__ __forceinline__ double alpha_term(cx<T> Hk, cx<T> Xk, int m, T invL, 
     return (k == kc) ? at : 2.0 * at;
 }
 
-// First pass source of the final transform of a pair job: Q_k = P_A,k + i P_B,k
-// computed on the fly from the spectra S1 = fft(h_A + i h_B), S2 = fft(x_A + i x_B).
-template <typename T>
-struct PairCombine {
-    const cx<T>* s1;
-    const cx<T>* s2;
-    int mA, mB, L;
-    T invL;
-    bool fp64;
-    __device__ __forceinline__ cx<T> operator()(int k) const {
-        const int kc = (k == 0) ? 0 : L - k;
-        cx<T> HA, HB, XA, XB;
-        unpack(s1[sp(k)], conjg(s1[sp(kc)]), HA, HB);
-        unpack(s2[sp(k)], conjg(s2[sp(kc)]), XA, XB);
-        double at;
-        const cx<T> PA = fp64 ? product<double>(HA, XA, mA, invL, at) : product<T>(HA, XA, mA, invL, at);
-        const cx<T> PB = fp64 ? product<double>(HB, XB, mB, invL, at) : product<T>(HB, XB, mB, invL, at);
-        return PA + mul_pi(PB);
-    }
-};
-
-// Same for a single job: S = fft(h + i x), Q_k = P_k.
-template <typename T>
-struct SingleCombine {
-    const cx<T>* s;
-    int m, L;
-    T invL;
-    bool fp64;
-    __device__ __forceinline__ cx<T> operator()(int k) const {
-        const int kc = (k == 0) ? 0 : L - k;
-        cx<T> Hk, Xk;
-        unpack(s[sp(k)], conjg(s[sp(kc)]), Hk, Xk);
-        double at;
-        return fp64 ? product<double>(Hk, Xk, m, invL, at) : product<T>(Hk, Xk, m, invL, at);
-    }
-};
-
 template <typename T>
 __global__ void __launch_bounds__(512) real_fwd_kernel(const RealJob* __restrict__ jobs, int first,
                                                         const T* __restrict__ h, const T* __restrict__ x,
@@ -144,57 +110,83 @@ __global__ void __launch_bounds__(512) real_fwd_kernel(const RealJob* __restrict
                                                         int Lmax, int flags) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* red = reinterpret_cast<double*>(smem_raw);
-    cx<T>* bA = reinterpret_cast<cx<T>*>(smem_raw + RED_BYTES);
+    cx<T>* tws = reinterpret_cast<cx<T>*>(smem_raw + RED_BYTES);
+    cx<T>* bA = tws + TW_SMEM;
     cx<T>* bB = bA + smem_elems(Lmax);
     cx<T>* bC = bB + smem_elems(Lmax);
     const RealJob J = jobs[first + blockIdx.x];
     const Group g{(int)threadIdx.x, (int)blockDim.x, 0};
     const FftPlan P = J.P;
     const int L = P.L;
-    const cx<T>* tw = tw_all + P.tw_off;
+    const TwTab<T> tw = load_twiddles(tws, tw_all + P.tw_off, L, g);
     const bool fp64 = (flags & HANKEL_FP64_POWER) != 0;
     const T invL = T(1) / T(L);
+    const PairSt<T> store{y + J.yA, J.nA, y + J.yB, J.single ? 0 : J.nB};
     double aA = 0.0, aB = 0.0;
+    cx<T>*S1, *F, *O;
 
+    g.sync();
     if (J.single) {
-        cx<T>* S = fft_smem<T>(P, PairLoad<T>{h + J.hA, J.dA, x + J.xA, J.nA}, bA, bB, tw, g);
-        cx<T>* F = (S == bA) ? bB : bA;
+        // S = fft(h~ + i x~); Q_k = ifft(h~)_k X_k^{m-1}
+        S1 = fft_stage<T>(P, GLd<T>{h + J.hA, J.dA, x + J.xA, J.nA}, nullptr, bA, bB, store, true, tw, g);
+        F = (S1 == bA) ? bB : bA;
         if (flags & HANKEL_STORE_SPECTRA)
-            for (int k = g.tid; k < L; k += g.nthr) ws[J.wsA + k] = S[sp(k)];
-        if (alpha != nullptr)
-            for (int k = g.tid; k <= L / 2; k += g.nthr) {
-                const int kc = (k == 0) ? 0 : L - k;
-                cx<T> Hk, Xk;
-                unpack(S[sp(k)], conjg(S[sp(kc)]), Hk, Xk);
-                aA += alpha_term(Hk, Xk, J.mA, invL, fp64, k, kc);
-            }
-        if (y != nullptr)
-            fft_out<T>(P, SingleCombine<T>{S, J.mA, L, invL, fp64}, F, S, PairStore<T>{y + J.yA, J.nA, nullptr, 0},
-                       tw, g);
+            for (int k = g.tid; k < L; k += g.nthr) ws[J.wsA + k] = S1[sp(k)];
+        for (int k = g.tid; k <= L / 2; k += g.nthr) {
+            const int kc = (k == 0) ? 0 : L - k;
+            cx<T> Hk, Xk;
+            unpack(S1[sp(k)], conjg(S1[sp(kc)]), Hk, Xk);
+            double at;
+            const cx<T> Pk = fp64 ? product<double>(Hk, Xk, J.mA, invL, at) : product<T>(Hk, Xk, J.mA, invL, at);
+            aA += (k == kc) ? at : 2.0 * at;
+            F[sp(k)] = Pk;
+            if (kc != k) F[sp(kc)] = conjg(Pk);
+        }
+        O = S1;
     } else {
-        cx<T>* S1 = fft_smem<T>(P, PairLoad<T>{h + J.hA, J.dA, h + J.hB, J.dB}, bA, bB, tw, g);
-        cx<T>* O = (S1 == bA) ? bB : bA;
-        cx<T>* S2 = fft_smem<T>(P, PairLoad<T>{x + J.xA, J.nA, x + J.xB, J.nB}, bC, O, tw, g);
-        cx<T>* F = (S2 == bC) ? O : bC;
-        if (alpha != nullptr)
-            for (int k = g.tid; k <= L / 2; k += g.nthr) {
-                const int kc = (k == 0) ? 0 : L - k;
-                cx<T> HA, HB, XA, XB;
-                unpack(S1[sp(k)], conjg(S1[sp(kc)]), HA, HB);
-                unpack(S2[sp(k)], conjg(S2[sp(kc)]), XA, XB);
-                aA += alpha_term(HA, XA, J.mA, invL, fp64, k, kc);
-                aB += alpha_term(HB, XB, J.mB, invL, fp64, k, kc);
+        // S1 = fft(h~_A + i h~_B), S2 = fft(x~_A + i x~_B); Q_k = P_A,k + i P_B,k
+        // both inputs stream into shared memory asynchronously; the x pair
+        // arrives while the h pair is being transformed
+        cp_async_pair(bA, h + J.hA, J.dA, h + J.hB, J.dB, L, g);
+        cp_async_pair(bC, x + J.xA, J.nA, x + J.xB, J.nB, L, g);
+        cp_wait<1>();
+        g.sync();
+        const GLd<T> none{nullptr, 0, nullptr, 0};
+        S1 = fft_stage<T>(P, none, bA, bB, bA, store, true, tw, g);
+        cx<T>* other = (S1 == bA) ? bB : bA;
+        cp_wait<0>();
+        g.sync();
+        cx<T>* S2 = fft_stage<T>(P, none, bC, other, bC, store, true, tw, g);
+        F = (S2 == bC) ? other : bC;
+        for (int k = g.tid; k <= L / 2; k += g.nthr) {
+            const int kc = (k == 0) ? 0 : L - k;
+            cx<T> HA, HB, XA, XB;
+            unpack(S1[sp(k)], conjg(S1[sp(kc)]), HA, HB);
+            unpack(S2[sp(k)], conjg(S2[sp(kc)]), XA, XB);
+            double atA, atB;
+            cx<T> PA, PB;
+            if (fp64) {
+                PA = product<double>(HA, XA, J.mA, invL, atA);
+                PB = product<double>(HB, XB, J.mB, invL, atB);
+            } else {
+                PA = product<T>(HA, XA, J.mA, invL, atA);
+                PB = product<T>(HB, XB, J.mB, invL, atB);
             }
-        if (y != nullptr)
-            fft_out<T>(P, PairCombine<T>{S1, S2, J.mA, J.mB, L, invL, fp64}, F, S1,
-                       PairStore<T>{y + J.yA, J.nA, y + J.yB, J.nB}, tw, g);
+            aA += (k == kc) ? atA : 2.0 * atA;
+            aB += (k == kc) ? atB : 2.0 * atB;
+            F[sp(k)] = PA + mul_pi(PB);
+            if (kc != k) F[sp(kc)] = conjg(PA) + mul_pi(conjg(PB));
+        }
+        O = S1;
     }
+    g.sync();
+    if (y != nullptr) fft_stage<T>(P, GLd<T>{nullptr, 0, nullptr, 0}, F, O, F, store, false, tw, g);
     if (alpha != nullptr) {
         const double sA = group_sum(aA, red, g);
         const double sB = J.single ? 0.0 : group_sum(aB, red, g);
         if (g.tid == 0) {
             alpha[J.iA] = (T)sA;
-            if (!J.single) alpha[J.iB] = (T)sB;
+            if (!J.single && J.iB >= 0) alpha[J.iB] = (T)sB;
         }
     }
 }
@@ -212,22 +204,6 @@ __device__ __forceinline__ cx<T> adjoint_bin(cx<T> U, cx<T> Wc, cx<T> G, int m, 
     return mk<T>((T)(qh.x - qx.y), (T)(qh.y + qx.x));   // qh + i qx
 }
 
-// First pass source of the adjoint transform: U = fft(h + i x) in global
-// workspace, G = fft(g) in shared memory.
-template <typename T>
-struct AdjCombine {
-    const cx<T>* U;
-    const cx<T>* G;
-    int m, L;
-    T invL;
-    bool fp64;
-    __device__ __forceinline__ cx<T> operator()(int k) const {
-        const int kc = (k == 0) ? 0 : L - k;
-        const cx<T> Uk = U[k], Uc = conjg(U[kc]), Gk = G[sp(k)];
-        return fp64 ? adjoint_bin<double>(Uk, Uc, Gk, m, invL) : adjoint_bin<T>(Uk, Uc, Gk, m, invL);
-    }
-};
-
 template <typename T>
 __global__ void __launch_bounds__(512) real_bwd_kernel(const RealJob* __restrict__ jobs, int first,
                                                         const T* __restrict__ gy, const T* __restrict__ h,
@@ -235,26 +211,44 @@ __global__ void __launch_bounds__(512) real_bwd_kernel(const RealJob* __restrict
                                                         T* __restrict__ gx, const cx<T>* __restrict__ tw_all,
                                                         cx<T>* ws, int Lmax, int flags, int stored) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cx<T>* bA = reinterpret_cast<cx<T>*>(smem_raw + RED_BYTES);
+    cx<T>* tws = reinterpret_cast<cx<T>*>(smem_raw + RED_BYTES);
+    cx<T>* bA = tws + TW_SMEM;
     cx<T>* bB = bA + smem_elems(Lmax);
     const RealJob J = jobs[first + blockIdx.x];
     const Group g{(int)threadIdx.x, (int)blockDim.x, 0};
     const FftPlan P = J.P;
     const int L = P.L;
-    const cx<T>* tw = tw_all + P.tw_off;
+    const TwTab<T> tw = load_twiddles(tws, tw_all + P.tw_off, L, g);
+    g.sync();
     const bool fp64 = (flags & HANKEL_FP64_POWER) != 0;
     const T invL = T(1) / T(L);
     cx<T>* U = ws + J.wsA;
 
-    if (!stored) {
-        cx<T>* S = fft_smem<T>(P, PairLoad<T>{h + J.hA, J.dA, x + J.xA, J.nA}, bA, bB, tw, g);
-        for (int k = g.tid; k < L; k += g.nthr) U[k] = S[sp(k)];
-        g.sync();
-    }
-    cx<T>* G = fft_smem<T>(P, PairLoad<T>{gy + J.yA, J.nA, nullptr, 0}, bA, bB, tw, g);
+    // U = fft(h~ + i x~) straight to workspace (or kept from the forward call)
+    if (!stored) fft_stage<T>(P, GLd<T>{h + J.hA, J.dA, x + J.xA, J.nA}, nullptr, bA, bB, GSt<T>{U}, false, tw, g);
+    const AdjSt<T> store{gh ? gh + J.hA : nullptr, J.dA, gx ? gx + J.xA : nullptr, J.nA, L};
+    cx<T>* G = fft_stage<T>(P, GLd<T>{gy + J.yA, J.nA, nullptr, 0}, nullptr, bA, bB, store, true, tw, g);
     cx<T>* F = (G == bA) ? bB : bA;
-    fft_out<T>(P, AdjCombine<T>{U, G, J.mA, L, invL, fp64}, F, G,
-               AdjStore<T>{gh ? gh + J.hA : nullptr, J.dA, gx ? gx + J.xA : nullptr, J.nA, L}, tw, g);
+    for (int k = g.tid; k < L; k += g.nthr) {
+        const int kc = (k == 0) ? 0 : L - k;
+        const cx<T> Uk = U[k], Uc = conjg(U[kc]), Gk = G[sp(k)];
+        F[sp(k)] = fp64 ? adjoint_bin<double>(Uk, Uc, Gk, J.mA, invL) : adjoint_bin<T>(Uk, Uc, Gk, J.mA, invL);
+    }
+    g.sync();
+    fft_stage<T>(P, GLd<T>{nullptr, 0, nullptr, 0}, F, G, F, store, false, tw, g);
+}
+
+// Two-level twiddle table of length L (fft_stage.cuh): A[j] = w_L^{64 j},
+// B[j] = w_L^j, from FP64 sincospi rounded to T.
+template <typename T>
+__global__ void stage_twiddle_kernel(cx<T>* out, int L) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nA = (L + TW_LO - 1) / TW_LO;
+    if (e >= nA + TW_LO) return;
+    const long long j = (e < nA) ? (long long)e * TW_LO : (long long)(e - nA);
+    double s, c;
+    sincospi(-2.0 * (double)(j % L) / (double)L, &s, &c);
+    out[e] = mk<T>((T)c, (T)s);
 }
 
 template <typename T>
@@ -271,7 +265,7 @@ __global__ void twiddle_kernel(cx<T>* out, int L) {
 
 template <typename T>
 static size_t real_smem_bytes(const RealLaunch& lc) {
-    return RED_BYTES + (size_t)lc.arrays * smem_elems(lc.Lmax) * sizeof(cx<T>);
+    return RED_BYTES + ((size_t)TW_SMEM + (size_t)lc.arrays * smem_elems(lc.Lmax)) * sizeof(cx<T>);
 }
 
 template <typename T>
@@ -320,6 +314,18 @@ cudaError_t launch_twiddles(bool dbl, void* out, int L, cudaStream_t st) {
         twiddle_kernel<float><<<nb, 256, 0, st>>>((cx<float>*)out, L);
     return cudaGetLastError();
 }
+
+cudaError_t launch_stage_twiddles(bool dbl, void* out, const FftPlan& P, cudaStream_t st) {
+    const int total = tw_table_elems(P.L);
+    const int nb = (total + 255) / 256;
+    if (dbl)
+        stage_twiddle_kernel<double><<<nb, 256, 0, st>>>((cx<double>*)out, P.L);
+    else
+        stage_twiddle_kernel<float><<<nb, 256, 0, st>>>((cx<float>*)out, P.L);
+    return cudaGetLastError();
+}
+
+int stage_twiddle_count(const FftPlan& P) { return tw_table_elems(P.L); }
 
 size_t real_launch_smem(bool dbl, const RealLaunch& lc) {
     return dbl ? real_smem_bytes<double>(lc) : real_smem_bytes<float>(lc);

@@ -160,6 +160,44 @@ __device__ __forceinline__ void pass_st(const Src& src, const Dst& dst, int L, i
     }
 }
 
+// Shared -> shared pass when nb = L/R and Ns are multiples of 16: the padded
+// index is then linear in r (sp(i + r s) = sp(i) + r (s + s/16)), so each
+// butterfly computes one address per side.
+template <typename T, int R>
+__device__ __forceinline__ void pass_lin(const cx<T>* __restrict__ s, cx<T>* __restrict__ d, int L, int Ns,
+                                         unsigned magic, const TwTab<T>& tw, const Group& g) {
+    const int nb = L / R;
+    const int twstride = L / (Ns * R);
+    const int rs = nb + (nb >> 4), ws = Ns + (Ns >> 4);
+    for (int b = g.tid; b < nb; b += g.nthr) {
+        cx<T> v[R];
+        const cx<T>* sb = s + sp(b);
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = sb[r * rs];
+        const int k = mod_magic(b, Ns, magic);
+        apply_twiddles<T, R>(v, tw(k * twstride));
+        DFT<T, R>::run(v);
+        cx<T>* db = d + sp((b - k) * R + k);
+#pragma unroll
+        for (int r = 0; r < R; ++r) db[r * ws] = v[r];
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void pass_lin_sel(int R, const cx<T>* s, cx<T>* d, int L, int Ns, unsigned magic,
+                                             const TwTab<T>& tw, const Group& g) {
+    switch (R) {
+        case 16: pass_lin<T, 16>(s, d, L, Ns, magic, tw, g); break;
+        case 8: pass_lin<T, 8>(s, d, L, Ns, magic, tw, g); break;
+        case 4: pass_lin<T, 4>(s, d, L, Ns, magic, tw, g); break;
+        case 2: pass_lin<T, 2>(s, d, L, Ns, magic, tw, g); break;
+        case 3: pass_lin<T, 3>(s, d, L, Ns, magic, tw, g); break;
+        case 5: pass_lin<T, 5>(s, d, L, Ns, magic, tw, g); break;
+        case 7: pass_lin<T, 7>(s, d, L, Ns, magic, tw, g); break;
+        default: break;
+    }
+}
+
 template <typename T, class Src, class Dst>
 __device__ __forceinline__ void pass_sel(int R, const Src& src, const Dst& dst, int L, int Ns, unsigned magic,
                                          const TwTab<T>& tw, const Group& g) {
@@ -200,6 +238,8 @@ __device__ __noinline__ cx<T>* fft_stage(FftPlan P, GLd<T> gfirst, const cx<T>* 
         } else {
             if (to_last)
                 pass_sel<T>(R, SLd<T>{sp_src}, last, P.L, Ns, magic, twp, g);
+            else if ((((P.L / R) | Ns) & 15) == 0)
+                pass_lin_sel<T>(R, sp_src, buf[p & 1], P.L, Ns, magic, twp, g);
             else
                 pass_sel<T>(R, SLd<T>{sp_src}, SSt<T>{buf[p & 1]}, P.L, Ns, magic, twp, g);
         }

@@ -83,11 +83,11 @@ __device__ __forceinline__ void unpack(cx<T> u, cx<T> w_conj, cx<T>& a, cx<T>& b
 // Spectral product of one tensor at bin k: P = ifft(h~)_k X_k^{m-1}, plus the
 // alpha term ifft(h~)_k X_k^m; formed in A precision.
 template <typename A, typename T>
-__device__ __forceinline__ cx<T> product(cx<T> Hk, cx<T> Xk, int m, T invL, double& aterm) {
+__device__ __forceinline__ cx<T> product(cx<T> Hk, cx<T> Xk, int m, T invL, double& aterm, bool want_alpha = true) {
     const cx<A> hh = scal(up<A>(conjg(Hk)), (A)invL);
     const cx<A> X = up<A>(Xk);
     const cx<A> p = times_pow(hh, X, m - 1);
-    aterm = (double)cmul(p, X).x;
+    aterm = want_alpha ? (double)cmul(p, X).x : 0.0;
     return mk<T>((T)p.x, (T)p.y);
 }
 
@@ -137,8 +137,10 @@ __global__ void __launch_bounds__(512) real_fwd_kernel(const RealJob* __restrict
             cx<T> Hk, Xk;
             unpack(S1[sp(k)], conjg(S1[sp(kc)]), Hk, Xk);
             double at;
-            const cx<T> Pk = fp64 ? product<double>(Hk, Xk, J.mA, invL, at) : product<T>(Hk, Xk, J.mA, invL, at);
-            aA += (k == kc) ? at : 2.0 * at;
+            const bool wa = alpha != nullptr;
+            const cx<T> Pk =
+                fp64 ? product<double>(Hk, Xk, J.mA, invL, at, wa) : product<T>(Hk, Xk, J.mA, invL, at, wa);
+            if (wa) aA += (k == kc) ? at : 2.0 * at;
             F[sp(k)] = Pk;
             if (kc != k) F[sp(kc)] = conjg(Pk);
         }
@@ -165,15 +167,18 @@ __global__ void __launch_bounds__(512) real_fwd_kernel(const RealJob* __restrict
             unpack(S2[sp(k)], conjg(S2[sp(kc)]), XA, XB);
             double atA, atB;
             cx<T> PA, PB;
+            const bool wa = alpha != nullptr;
             if (fp64) {
-                PA = product<double>(HA, XA, J.mA, invL, atA);
-                PB = product<double>(HB, XB, J.mB, invL, atB);
+                PA = product<double>(HA, XA, J.mA, invL, atA, wa);
+                PB = product<double>(HB, XB, J.mB, invL, atB, wa);
             } else {
-                PA = product<T>(HA, XA, J.mA, invL, atA);
-                PB = product<T>(HB, XB, J.mB, invL, atB);
+                PA = product<T>(HA, XA, J.mA, invL, atA, wa);
+                PB = product<T>(HB, XB, J.mB, invL, atB, wa);
             }
-            aA += (k == kc) ? atA : 2.0 * atA;
-            aB += (k == kc) ? atB : 2.0 * atB;
+            if (wa) {
+                aA += (k == kc) ? atA : 2.0 * atA;
+                aB += (k == kc) ? atB : 2.0 * atB;
+            }
             F[sp(k)] = PA + mul_pi(PB);
             if (kc != k) F[sp(kc)] = conjg(PA) + mul_pi(conjg(PB));
         }

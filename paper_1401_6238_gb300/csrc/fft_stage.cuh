@@ -249,6 +249,47 @@ __device__ __noinline__ cx<T>* fft_stage(FftPlan P, GLd<T> gfirst, const cx<T>* 
     return keep ? buf[(P.npass - 1) & 1] : nullptr;
 }
 
+// Complex global buffer used as transform scratch (lengths beyond shared memory).
+template <typename T>
+struct CLd {
+    const cx<T>* p;
+    __device__ __forceinline__ cx<T> operator()(int i) const { return p[i]; }
+};
+
+// Transform through two global scratch buffers w0, w1 (L complex each):
+// pass 0 reads `gfirst` (zero-padded real pair) or `cfirst` when not null;
+// passes ping-pong between w0 (written by pass 0) and w1; the last pass
+// writes `last` unless `keep`, in which case the buffer holding the result
+// is returned.  Barriers between passes make each block's global writes
+// visible to its own threads.
+template <typename T, class Last>
+__device__ __noinline__ cx<T>* fft_global(FftPlan P, GLd<T> gfirst, const cx<T>* cfirst, cx<T>* w0, cx<T>* w1,
+                                          Last last, bool keep, TwTab<T> twp, Group g) {
+    cx<T>* buf[2] = {w0, w1};
+    int Ns = 1;
+    for (int p = 0; p < P.npass; ++p) {
+        const int R = P.radix[p];
+        const unsigned magic = (unsigned)((0x100000000ull + (unsigned)Ns - 1) / (unsigned)Ns);
+        const bool to_last = (p == P.npass - 1) && !keep;
+        const cx<T>* src = (p == 0) ? cfirst : buf[(p - 1) & 1];
+        if (src == nullptr) {
+            if (to_last)
+                pass_sel<T>(R, gfirst, last, P.L, Ns, magic, twp, g);
+            else
+                pass_sel<T>(R, gfirst, GSt<T>{buf[p & 1]}, P.L, Ns, magic, twp, g);
+        } else {
+            if (to_last)
+                pass_sel<T>(R, CLd<T>{src}, last, P.L, Ns, magic, twp, g);
+            else
+                pass_sel<T>(R, CLd<T>{src}, GSt<T>{buf[p & 1]}, P.L, Ns, magic, twp, g);
+        }
+        __threadfence_block();
+        g.sync();
+        Ns *= R;
+    }
+    return keep ? buf[(P.npass - 1) & 1] : nullptr;
+}
+
 // Copy the two-level twiddle table of length L from global memory into `dst`
 // (shared memory); returns the table view.  Caller synchronises.
 template <typename T>

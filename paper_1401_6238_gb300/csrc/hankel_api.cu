@@ -264,9 +264,12 @@ int max_len_for(int buffers, size_t csize) {
 // Group jobs into launches of one block size and one job kind each (pairs
 // need three shared buffers, singles two), largest transforms first.
 void make_launches(std::vector<hk::RealJob>& jobs, std::vector<hk::RealLaunch>& launches, bool one_per_launch,
-                   int single_buffers) {
-    std::stable_sort(jobs.begin(), jobs.end(), [](const hk::RealJob& a, const hk::RealJob& b) {
-        if (a.single != b.single) return a.single < b.single;
+                   int single_buffers, int max_single_L) {
+    // kind: 0 pair (three shared buffers), 1 single (two), 2 single with
+    // global scratch (shared memory holds only twiddles)
+    auto kind = [&](const hk::RealJob& j) { return !j.single ? 0 : (j.P.L > max_single_L ? 2 : 1); };
+    std::stable_sort(jobs.begin(), jobs.end(), [&](const hk::RealJob& a, const hk::RealJob& b) {
+        if (kind(a) != kind(b)) return kind(a) < kind(b);
         return a.P.L > b.P.L;
     });
     launches.clear();
@@ -277,10 +280,10 @@ void make_launches(std::vector<hk::RealJob>& jobs, std::vector<hk::RealLaunch>& 
         lc.nthr = nthr_of(L0);
         lc.emax = 0;
         lc.Lmax = L0;
-        lc.arrays = jobs[i].single ? single_buffers : 3;
+        lc.arrays = kind(jobs[i]) == 0 ? 3 : (kind(jobs[i]) == 1 ? single_buffers : 0);
         size_t j = i + 1;
         if (!one_per_launch)
-            while (j < jobs.size() && nthr_of(jobs[j].P.L) == lc.nthr && jobs[j].single == jobs[i].single) ++j;
+            while (j < jobs.size() && nthr_of(jobs[j].P.L) == lc.nthr && kind(jobs[j]) == kind(jobs[i])) ++j;
         lc.count = (int)(j - i);
         launches.push_back(lc);
         i = j;
@@ -303,23 +306,27 @@ hankel_status build_real_path(hankel_plan_s* p) {
     const size_t cs = 2 * real_size(p->dtype);
     const int max_pair_L = max_len_for(3, cs);
     const int max_single_L = max_len_for(2, cs);
-    for (int64_t i = 0; i < count; ++i)
-        if (p->Lof[i] > max_single_L)
-            return fail(HANKEL_EUNSUPPORTED, "descriptor %lld: FFT length %d exceeds the shared-memory limit %d of "
-                        "this build for this dtype", (long long)i, p->Lof[i], max_single_L);
     const bool singles = (p->flags & (HANKEL_STORE_SPECTRA | HANKEL_ONE_PER_LAUNCH)) != 0;
-    std::vector<int64_t> ws_off(count);
+    // workspace: one spectrum (L) per tensor, then 2 L of transform scratch
+    // for each tensor longer than shared memory allows
+    std::vector<int64_t> ws_off(count), gscratch(count, -1);
     int64_t ws = 0;
     for (int64_t i = 0; i < count; ++i) {
         ws_off[i] = ws;
         ws += p->Lof[i];
     }
+    for (int64_t i = 0; i < count; ++i)
+        if (p->Lof[i] > max_single_L) {
+            gscratch[i] = ws;
+            ws += 2 * (int64_t)p->Lof[i];
+        }
     auto fill = [&](hk::RealJob& J, int64_t i, bool B) {
         const hankel_desc& d = p->descs[i];
         const int dl = (int)(d.n[0] * (int64_t)d.m - d.m + 1);
         if (!B) {
             J.mA = d.m; J.nA = d.n[0]; J.dA = dl; J.iA = (int)i;
             J.hA = d.h_off; J.xA = d.x_off[0]; J.yA = d.y_off; J.wsA = ws_off[i];
+            if (gscratch[i] >= 0) J.wsB = gscratch[i];
         } else {
             J.mB = d.m; J.nB = d.n[0]; J.dB = dl; J.iB = (int)i;
             J.hB = d.h_off; J.xB = d.x_off[0]; J.yB = d.y_off; J.wsB = ws_off[i];
@@ -363,8 +370,8 @@ hankel_status build_real_path(hankel_plan_s* p) {
         p->bwd_jobs.push_back(J);
     }
     const bool opl = (p->flags & HANKEL_ONE_PER_LAUNCH) != 0;
-    make_launches(p->fwd_jobs, p->fwd_launches, opl, 2);
-    make_launches(p->bwd_jobs, p->bwd_launches, opl, 2);
+    make_launches(p->fwd_jobs, p->fwd_launches, opl, 2, max_single_L);
+    make_launches(p->bwd_jobs, p->bwd_launches, opl, 2, max_single_L);
     for (auto* v : {&p->fwd_launches, &p->bwd_launches})
         for (auto& lc : *v)
             if (hk::real_launch_smem(dbl, lc) > kSmemLimit)

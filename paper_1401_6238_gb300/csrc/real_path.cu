@@ -243,6 +243,87 @@ __global__ void __launch_bounds__(512) real_bwd_kernel(const RealJob* __restrict
     fft_stage<T>(P, GLd<T>{nullptr, 0, nullptr, 0}, F, G, F, store, false, tw, g);
 }
 
+// Single jobs whose transforms exceed shared memory: the same steps with
+// the transform scratch in global workspace (two L-buffers per job at wsB,
+// L2-resident in practice); shared memory holds only the twiddle table.
+template <typename T>
+__global__ void __launch_bounds__(512) real_fwd_global_kernel(const RealJob* __restrict__ jobs, int first,
+                                                               const T* __restrict__ h, const T* __restrict__ x,
+                                                               T* __restrict__ y, T* __restrict__ alpha,
+                                                               const cx<T>* __restrict__ tw_all, cx<T>* ws,
+                                                               int flags) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* red = reinterpret_cast<double*>(smem_raw);
+    cx<T>* tws = reinterpret_cast<cx<T>*>(smem_raw + RED_BYTES);
+    const RealJob J = jobs[first + blockIdx.x];
+    const Group g{(int)threadIdx.x, (int)blockDim.x, 0};
+    const FftPlan P = J.P;
+    const int L = P.L;
+    const TwTab<T> tw = load_twiddles(tws, tw_all + P.tw_off, L, g);
+    g.sync();
+    const bool fp64 = (flags & HANKEL_FP64_POWER) != 0;
+    const T invL = T(1) / T(L);
+    cx<T>* W0 = ws + J.wsB;
+    cx<T>* W1 = W0 + L;
+    const PairSt<T> store{y + J.yA, J.nA, nullptr, 0};
+    cx<T>* S = fft_global<T>(P, GLd<T>{h + J.hA, J.dA, x + J.xA, J.nA}, nullptr, W0, W1, store, true, tw, g);
+    cx<T>* F = (S == W0) ? W1 : W0;
+    if (flags & HANKEL_STORE_SPECTRA)
+        for (int k = g.tid; k < L; k += g.nthr) ws[J.wsA + k] = S[k];
+    double aA = 0.0;
+    const bool wa = alpha != nullptr;
+    for (int k = g.tid; k <= L / 2; k += g.nthr) {
+        const int kc = (k == 0) ? 0 : L - k;
+        cx<T> Hk, Xk;
+        unpack(S[k], conjg(S[kc]), Hk, Xk);
+        double at;
+        const cx<T> Pk = fp64 ? product<double>(Hk, Xk, J.mA, invL, at, wa) : product<T>(Hk, Xk, J.mA, invL, at, wa);
+        if (wa) aA += (k == kc) ? at : 2.0 * at;
+        F[k] = Pk;
+        if (kc != k) F[kc] = conjg(Pk);
+    }
+    __threadfence_block();
+    g.sync();
+    if (y != nullptr) fft_global<T>(P, GLd<T>{nullptr, 0, nullptr, 0}, F, S, F, store, false, tw, g);
+    if (wa) {
+        const double sA = group_sum(aA, red, g);
+        if (g.tid == 0) alpha[J.iA] = (T)sA;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) real_bwd_global_kernel(const RealJob* __restrict__ jobs, int first,
+                                                               const T* __restrict__ gy, const T* __restrict__ h,
+                                                               const T* __restrict__ x, T* __restrict__ gh,
+                                                               T* __restrict__ gx, const cx<T>* __restrict__ tw_all,
+                                                               cx<T>* ws, int flags, int stored) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T>* tws = reinterpret_cast<cx<T>*>(smem_raw + RED_BYTES);
+    const RealJob J = jobs[first + blockIdx.x];
+    const Group g{(int)threadIdx.x, (int)blockDim.x, 0};
+    const FftPlan P = J.P;
+    const int L = P.L;
+    const TwTab<T> tw = load_twiddles(tws, tw_all + P.tw_off, L, g);
+    g.sync();
+    const bool fp64 = (flags & HANKEL_FP64_POWER) != 0;
+    const T invL = T(1) / T(L);
+    cx<T>* U = ws + J.wsA;
+    cx<T>* W0 = ws + J.wsB;
+    cx<T>* W1 = W0 + L;
+    if (!stored) fft_global<T>(P, GLd<T>{h + J.hA, J.dA, x + J.xA, J.nA}, nullptr, W0, W1, GSt<T>{U}, false, tw, g);
+    const AdjSt<T> store{gh ? gh + J.hA : nullptr, J.dA, gx ? gx + J.xA : nullptr, J.nA, L};
+    cx<T>* G = fft_global<T>(P, GLd<T>{gy + J.yA, J.nA, nullptr, 0}, nullptr, W0, W1, store, true, tw, g);
+    cx<T>* F = (G == W0) ? W1 : W0;
+    for (int k = g.tid; k < L; k += g.nthr) {
+        const int kc = (k == 0) ? 0 : L - k;
+        const cx<T> Uk = U[k], Uc = conjg(U[kc]), Gk = G[k];
+        F[k] = fp64 ? adjoint_bin<double>(Uk, Uc, Gk, J.mA, invL) : adjoint_bin<T>(Uk, Uc, Gk, J.mA, invL);
+    }
+    __threadfence_block();
+    g.sync();
+    fft_global<T>(P, GLd<T>{nullptr, 0, nullptr, 0}, F, G, F, store, false, tw, g);
+}
+
 // Two-level twiddle table of length L (fft_stage.cuh): A[j] = w_L^{64 j},
 // B[j] = w_L^j, from FP64 sincospi rounded to T.
 template <typename T>
@@ -277,6 +358,11 @@ template <typename T>
 static cudaError_t launch_fwd_t(const RealLaunch& lc, const RealJob* jobs, const void* h, const void* x, void* y,
                                 void* alpha, const void* tw, void* ws, int flags, cudaStream_t st) {
     const size_t smem = real_smem_bytes<T>(lc);
+    if (lc.arrays == 0) {
+        real_fwd_global_kernel<T><<<lc.count, lc.nthr, smem, st>>>(jobs, lc.first, (const T*)h, (const T*)x, (T*)y,
+                                                                   (T*)alpha, (const cx<T>*)tw, (cx<T>*)ws, flags);
+        return cudaGetLastError();
+    }
     auto k = real_fwd_kernel<T>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -290,6 +376,12 @@ static cudaError_t launch_bwd_t(const RealLaunch& lc, const RealJob* jobs, const
                                 const void* x, void* gh, void* gx, const void* tw, void* ws, int flags, int stored,
                                 cudaStream_t st) {
     const size_t smem = real_smem_bytes<T>(lc);
+    if (lc.arrays == 0) {
+        real_bwd_global_kernel<T><<<lc.count, lc.nthr, smem, st>>>(jobs, lc.first, (const T*)gy, (const T*)h,
+                                                                   (const T*)x, (T*)gh, (T*)gx, (const cx<T>*)tw,
+                                                                   (cx<T>*)ws, flags, stored);
+        return cudaGetLastError();
+    }
     auto k = real_bwd_kernel<T>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

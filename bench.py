@@ -127,6 +127,95 @@ def read_clocks(path, proc, gpu_index):
             "samples": len(sm)}
 
 
+def timed(fn, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def secondary_workloads(dev, stream, steps=10, warmup=3):
+    """The other workloads of the path, timed on the device (inputs resident;
+    these batches are L2-sized, so they measure the kernels, not HBM)."""
+    import torch
+    from paper_1401_6238_gb300 import hankel as hk
+    from paper_1401_6238_gb300 import workloads as wl
+    out = {}
+    # gradient workload: loss through y = H x^{m-1}, m = 4, n = 4096, batch 64
+    b = wl.grad_case(batch=64, m=4, n=4096, seed=3)
+    plan = hk.Plan(hk.batch_descs(b), hk.R32, hk.SAME_X | hk.STORE_SPECTRA)
+    f32 = lambda a: torch.tensor(a, dtype=torch.float32, device=dev)
+    H, X = f32(b.h), f32(b.x)
+    Y = torch.zeros(plan.info["y_elems"], dtype=torch.float32, device=dev)
+    G = f32(np.random.default_rng(0).standard_normal(plan.info["y_elems"]))
+    gh, gx = torch.zeros_like(H), torch.zeros_like(X)
+
+    def grad_step():
+        plan.txv(H, X, Y, None, stream)
+        plan.backward(G, H, X, gh, gx, stream)
+
+    ms = timed(grad_step, steps, warmup, stream)
+    out["grad"] = {"workload": "m=4, n=4096 (d=16381, L=16384), batch 64, FP32 forward + backward (spectra kept)",
+                   "value": 64 / (ms / 1e3), "unit": "forward+backward products/s", "ms_per_step": ms}
+    plan.close()
+    # HOOI tensor-matrix products: 16 x 16 column pairs, shared h, complex64
+    R, N = 16, 4094
+    s = wl.edf_1d_signal(N=N, seed=4)
+    dims = [N + 2 - 2 * ((N + 2) // 3), (N + 2) // 3, (N + 2) // 3]
+    U = wl.unit_columns(dims[1], R, seed=5)
+    V = wl.unit_columns(dims[2], R, seed=6)
+    descs = hk.make_descs(R * R)
+    for k in range(R * R):
+        i, j = divmod(k, R)
+        descs[k]["m"] = 3
+        descs[k]["n"][:3] = dims
+        descs[k]["x_off"][1] = i * dims[1]
+        descs[k]["x_off"][2] = R * dims[1] + j * dims[2]
+        descs[k]["y_off"] = k * dims[0]
+    plan = hk.Plan(descs, hk.C64, 0)
+    c64 = lambda a: torch.tensor(a, dtype=torch.complex64, device=dev)
+    Hs, Xs = c64(s), c64(np.concatenate([U.T.reshape(-1), V.T.reshape(-1)]))
+    Ys = torch.zeros(R * R * dims[0], dtype=torch.complex64, device=dev)
+    ms = timed(lambda: plan.txv(Hs, Xs, Ys, None, stream), steps, warmup, stream)
+    out["hooi_products"] = {"workload": "complex64 order-3 Hankel of a length-4094 exponential signal "
+                                        "(1366 x 1365 x 1365), 16 x 16 column pairs H x2 u_i x3 v_j",
+                            "value": R * R / (ms / 1e3), "unit": "products/s", "ms_per_step": ms}
+    plan.close()
+    # 2D block (BHHB) products: 256 x 256 signal, blocks 86^3 x 86^3, 32 triples
+    count = 32
+    S = wl.edf_2d_signal(seed=5)
+    Xb = wl.unit_matrices(2 * count, 86, 86, seed=6)
+    descs = hk.make_descs(count)
+    for t in range(count):
+        descs[t]["m"] = 3
+        descs[t]["n"][:3] = 86
+        descs[t]["N"][:3] = 86
+        descs[t]["x_off"][1] = (2 * t) * 86 * 86
+        descs[t]["x_off"][2] = (2 * t + 1) * 86 * 86
+        descs[t]["y_off"] = t * 86 * 86
+    plan = hk.Plan(descs, hk.C64, hk.BLOCK)
+    Hb = c64(S.reshape(-1, order="F"))
+    Xv = c64(np.concatenate([X.reshape(-1, order="F") for X in Xb]))
+    Yb = torch.zeros(count * 86 * 86, dtype=torch.complex64, device=dev)
+    Gb = c64(np.random.default_rng(1).standard_normal(count * 86 * 86))
+    ghb, gxb = torch.zeros_like(Hb), torch.zeros_like(Xv)
+    ms_f = timed(lambda: plan.txv_block(Hb, Xv, Yb, None, stream), steps, warmup, stream)
+    ms_b = timed(lambda: plan.backward(Gb, Hb, Xv, ghb, gxb, stream), steps, warmup, stream)
+    out["bhhb"] = {"workload": "complex64 256 x 256 2D exponential signal, BHHB blocks (86,86,86) x (86,86,86), "
+                               "32 vector triples, forward and adjoint",
+                   "value": count / ((ms_f + ms_b) / 1e3), "unit": "forward+adjoint products/s",
+                   "forward_ms": ms_f, "adjoint_ms": ms_b}
+    plan.close()
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -165,6 +254,7 @@ def main():
     ap.add_argument("--copies", type=int, default=6)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the secondary workloads")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -299,6 +389,10 @@ def main():
                 "fp32_vs_fp64_max_rel_err": worst}
         p64.close()
 
+    secondary = None
+    if not args.no_secondary and rank == 0:
+        secondary = secondary_workloads(dev, stream)
+
     cpu = None
     if pool is not None:
         v, n, dt = cpu_oracle(seconds=15.0, pool=pool, cores=cores)
@@ -320,6 +414,7 @@ def main():
                              "algorithmic_bytes_per_step": alg_bytes},
                 "e2e": e2e, "gpu_launches": int(info["launches"]) * args.steps,
                 "plan": info, "fp64_plain": fp64, "cpu_baseline": cpu, "clocks": clocks,
+                "secondary": secondary,
                 "step_ms_min": float(np.min(step_ms)), "step_ms_median": float(np.median(step_ms))}
         print(json.dumps(line))
     plan.close()

@@ -40,6 +40,17 @@ template <typename T>
 __device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
 template <typename T>
 __device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+// FP32 complex add / subtract as one packed f32x2 operation each
+// (sm_100 family); FP64 stays scalar.
+__device__ __forceinline__ cx<float> operator+(cx<float> a, cx<float> b) {
+    const float2 r = __fadd2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y));
+    return mk<float>(r.x, r.y);
+}
+__device__ __forceinline__ cx<float> operator-(cx<float> a, cx<float> b) {
+    const float2 r = __ffma2_rn(make_float2(b.x, b.y), make_float2(-1.f, -1.f), make_float2(a.x, a.y));
+    return mk<float>(r.x, r.y);
+}
+
 template <typename T>
 __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
     return mk<T>(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));

@@ -145,8 +145,8 @@ __device__ __forceinline__ void apply_twiddles(cx<T>* v, cx<T> w) {
 template <typename T, int R, class Src, class Dst>
 __device__ __forceinline__ void pass_st(const Src& src, const Dst& dst, int L, int Ns, unsigned magic,
                                         const TwTab<T>& tw, const Group& g) {
-    const int nb = L / R;
-    const int twstride = L / (Ns * R);
+    const int nb = L / R;  // compile-time divisor
+    const int twstride = (Ns > 1) ? (int)__umulhi((unsigned)nb, magic) : nb;  // L / (Ns R), exact as Ns | nb
     for (int b = g.tid; b < nb; b += g.nthr) {
         cx<T> v[R];
 #pragma unroll
@@ -167,7 +167,7 @@ template <typename T, int R>
 __device__ __forceinline__ void pass_lin(const cx<T>* __restrict__ s, cx<T>* __restrict__ d, int L, int Ns,
                                          unsigned magic, const TwTab<T>& tw, const Group& g) {
     const int nb = L / R;
-    const int twstride = L / (Ns * R);
+    const int twstride = (int)__umulhi((unsigned)nb, magic);  // L / (Ns R), Ns >= 16 here
     const int rs = nb + (nb >> 4), ws = Ns + (Ns >> 4);
     for (int b = g.tid; b < nb; b += g.nthr) {
         cx<T> v[R];
@@ -227,7 +227,7 @@ __device__ __noinline__ cx<T>* fft_stage(FftPlan P, GLd<T> gfirst, const cx<T>* 
     int Ns = 1;
     for (int p = 0; p < P.npass; ++p) {
         const int R = P.radix[p];
-        const unsigned magic = (unsigned)((0x100000000ull + (unsigned)Ns - 1) / (unsigned)Ns);
+        const unsigned magic = P.magic[p];
         const bool to_last = (p == P.npass - 1) && !keep;
         const cx<T>* sp_src = (p == 0) ? sfirst : buf[(p - 1) & 1];
         if (sp_src == nullptr) {
@@ -269,7 +269,7 @@ __device__ __noinline__ cx<T>* fft_global(FftPlan P, GLd<T> gfirst, const cx<T>*
     int Ns = 1;
     for (int p = 0; p < P.npass; ++p) {
         const int R = P.radix[p];
-        const unsigned magic = (unsigned)((0x100000000ull + (unsigned)Ns - 1) / (unsigned)Ns);
+        const unsigned magic = P.magic[p];
         const bool to_last = (p == P.npass - 1) && !keep;
         const cx<T>* src = (p == 0) ? cfirst : buf[(p - 1) & 1];
         if (src == nullptr) {

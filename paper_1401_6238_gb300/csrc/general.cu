@@ -302,6 +302,7 @@ FftPlan plan_for(GeneralPlan* g, int L) {
     std::sort(rs.begin(), rs.end(), [](int x, int y) { return x > y; });
     P.npass = (int)rs.size();
     for (int i = 0; i < P.npass && i < 8; ++i) P.radix[i] = (uint8_t)rs[i];
+    fill_magic(P);
     return P;
 }
 

@@ -44,6 +44,13 @@ size_t elem_size(hankel_dtype d) { return real_size(d) * (is_complex(d) ? 2 : 1)
 // (shared-memory round trip + butterfly arithmetic, FP32 operations / point).
 constexpr int kMaxL = 16384;
 constexpr double kPassCost = 10.0;
+#ifndef HK_MAX16
+#define HK_MAX16 64
+#endif
+constexpr int kMax16 = HK_MAX16;  // radix-16 passes allowed per length
+#ifndef HK_THREAD_DIV
+#define HK_THREAD_DIV 16
+#endif
 double radix_cost(int r) {
     switch (r) {
         case 2: return 5.0;
@@ -75,7 +82,7 @@ bool factor(int L, std::vector<int>& out, double& cost) {
     // split a into parts of size 4,3,2,1 (log2 of 16,8,4,2)
     double best = 1e18;
     std::vector<int> bestp;
-    for (int n4 = 0; n4 * 4 <= a; ++n4)
+    for (int n4 = 0; n4 * 4 <= a && n4 <= kMax16; ++n4)
         for (int n3 = 0; n4 * 4 + n3 * 3 <= a; ++n3)
             for (int n2 = 0; n4 * 4 + n3 * 3 + n2 * 2 <= a; ++n2) {
                 int n1 = a - n4 * 4 - n3 * 3 - n2 * 2;
@@ -150,6 +157,7 @@ bool fft_factor(int L, FftPlan* P) {
     P->L = L;
     P->npass = (int)li->radix.size();
     for (int i = 0; i < P->npass && i < 8; ++i) P->radix[i] = (uint8_t)li->radix[i];
+    fill_magic(*P);
     return true;
 }
 // Record the message hankel_last_error() returns for this thread.
@@ -248,7 +256,7 @@ hankel_status upload_twiddles(hankel_plan_s* p, const std::vector<int>& Ls) {
 
 // Threads per block for a transform of length L: about one radix-16
 // butterfly per thread and pass, between one warp and 512 threads.
-int nthr_of(int L) { return std::max(32, std::min(512, pow2ceil((L + 15) / 16))); }
+int nthr_of(int L) { return std::max(32, std::min(512, pow2ceil((L + HK_THREAD_DIV - 1) / HK_THREAD_DIV))); }
 
 // Largest L whose `buffers` ping-pong arrays fit in one block's shared memory.
 constexpr size_t kSmemLimit = 227 * 1024;
@@ -297,6 +305,7 @@ hk::FftPlan fft_plan_of(const hankel_plan_s* p, int L) {
     P.npass = (int)li->radix.size();
     P.tw_off = p->tw_off.at(L);
     for (int i = 0; i < 8; ++i) P.radix[i] = i < P.npass ? (uint8_t)li->radix[i] : 0;
+    hk::fill_magic(P);
     return P;
 }
 

@@ -8,11 +8,22 @@
 namespace hk {
 
 // Plan of one length-L forward transform: L = radix[0] * ... * radix[npass-1],
-// twiddles exp(-2 pi i j / L), j < L, at tw_off in the plan's twiddle array.
+// twiddles at tw_off in the plan's twiddle array; magic[p] = ceil(2^32 / Ns_p)
+// with Ns_p = radix[0] * ... * radix[p-1], so that b mod Ns_p is a
+// multiply-high (exact for b * Ns_p < 2^32).
 struct FftPlan {
     int32_t L, npass, tw_off;
     uint8_t radix[8];
+    uint32_t magic[8];
 };
+
+inline void fill_magic(FftPlan& P) {
+    uint64_t Ns = 1;
+    for (int p = 0; p < 8; ++p) {
+        P.magic[p] = (p < P.npass) ? (uint32_t)((0x100000000ull + Ns - 1) / Ns) : 0u;
+        if (p < P.npass) Ns *= P.radix[p];
+    }
+}
 
 // Real square tensors with one vector per tensor (y = H x^{m-1}).  A job is
 // either a pair (A, B) of tensors with the same L -- two real problems share

@@ -286,23 +286,8 @@ int64_t fft_len(int64_t d) { return hankel_fft_length(d); }
 FftPlan plan_for(GeneralPlan* g, int L) {
     FftPlan P;
     std::memset(&P, 0, sizeof(P));
-    P.L = L;
+    fft_factor(L, &P);  // the planner's pass sequence for this length
     P.tw_off = g->tw_off.at(L);
-    // factorisation of L: same radix policy as the real path
-    int v = L, a = 0;
-    while (v % 2 == 0) { v /= 2; ++a; }
-    std::vector<int> rs;
-    while (a >= 4 && !(a == 5)) { rs.push_back(16); a -= 4; }
-    if (a == 5) { rs.push_back(8); rs.push_back(4); a = 0; }
-    if (a == 3) rs.push_back(8);
-    if (a == 2) rs.push_back(4);
-    if (a == 1) rs.push_back(2);
-    for (int p : {3, 5, 7})
-        while (v % p == 0) { v /= p; rs.push_back(p); }
-    std::sort(rs.begin(), rs.end(), [](int x, int y) { return x > y; });
-    P.npass = (int)rs.size();
-    for (int i = 0; i < P.npass && i < 8; ++i) P.radix[i] = (uint8_t)rs[i];
-    fill_magic(P);
     return P;
 }
 

@@ -127,6 +127,21 @@ def read_clocks(path, proc, gpu_index):
             "samples": len(sm)}
 
 
+def profiled_traffic():
+    """DRAM bytes per step of the forward kernel from the committed ncu
+    capture, or None when the kernel sources changed since it was taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "real_fwd_traffic.json")
+    try:
+        rec = json.load(open(path))
+        h = hashlib.sha256()
+        for f in rec["sources"]:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        return rec["bytes_per_step"] if h.hexdigest() == rec["sources_sha256"] else None
+    except Exception:
+        return None
+
+
 def timed(fn, steps, warmup, stream):
     import torch
     for _ in range(warmup):
@@ -331,13 +346,7 @@ def main():
     peak, peak_src = peaks()
     kernel_ms = float(np.mean(step_ms))
     achieved = alg_bytes / (kernel_ms / 1000.0) / 1e9
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "real_fwd_traffic.json")
-    if os.path.exists(tpath):
-        try:
-            traffic = json.load(open(tpath)).get("bytes_per_step")
-        except Exception:
-            traffic = None
+    traffic = profiled_traffic()
 
     # end to end through the host-buffer entry point
     hh = torch.tensor(batch.h, dtype=torch.float32).pin_memory()

@@ -67,9 +67,15 @@ struct AdjStore {
 template <typename A, typename T>
 __device__ __forceinline__ cx<A> up(cx<T> v) { return mk<A>((A)v.x, (A)v.y); }
 
+// p X^e for 0 <= e <= 7 by binary powering (straight-line, depth <= 3).
 template <typename A>
 __device__ __forceinline__ cx<A> times_pow(cx<A> p, cx<A> X, int e) {
-    for (int i = 0; i < e; ++i) p = cmul(p, X);
+    if (e & 1) p = cmul(p, X);
+    if (e & 6) {
+        const cx<A> X2 = cmul(X, X);
+        if (e & 2) p = cmul(p, X2);
+        if (e & 4) p = cmul(p, cmul(X2, X2));
+    }
     return p;
 }
 

@@ -29,7 +29,7 @@
 #include <tuple>
 #include <vector>
 
-#include "fft_core.cuh"
+#include "fft_stage.cuh"
 #include "general.h"
 #include "launch.h"
 
@@ -147,48 +147,43 @@ struct LineSink {
     }
 };
 
-// Transform `src` and store through `dst`.  When the sink overwrites the
-// line the source reads, the result is staged in shared memory first, so
-// that every read of the line finishes before the first write.
-template <typename T, class Src>
-__device__ __forceinline__ void line_run(const FftPlan& P, const Src& src, cx<T>* b0, cx<T>* b1,
-                                         const LineSink<T>& dst, bool inplace, const cx<T>* tw, const Group& g) {
-    if (inplace && P.npass == 1) {
-        cx<T>* r = fft_smem<T>(P, src, b0, b1, tw, g);
-        for (int i = g.tid; i < P.L; i += g.nthr) dst(i, r[sp(i)]);
-    } else {
-        fft_out<T>(P, src, b0, b1, dst, tw, g);
-    }
-}
+// shared-memory slots of the twiddle table (lengths up to 16384)
+constexpr int TWG_SMEM = tw_table_elems(16384);
 
+// One line per block: the line's input (an operand column/row, or a product
+// of spectral planes) is staged in shared memory, transformed by the stage
+// transform (fft_stage.cuh) and its prefix stored through the sink.  All
+// reads of the line finish before the first store, so a sink may overwrite
+// the line the source read.
 template <typename T>
 __global__ void __launch_bounds__(512) line_kernel(const LineTask* __restrict__ tasks, int first,
                                                    const void* __restrict__ in, void* out, cx<T>* ws,
                                                    const cx<T>* __restrict__ tw_all, int Lmax) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int64_t ops_s[MAXOPS];
-    cx<T>* b0 = reinterpret_cast<cx<T>*>(smem_raw + RED_BYTES);
+    cx<T>* tws = reinterpret_cast<cx<T>*>(smem_raw + RED_BYTES);
+    cx<T>* b0 = tws + TWG_SMEM;
     cx<T>* b1 = b0 + smem_elems(Lmax);
     const LineTask& t = tasks[first + blockIdx.x];
     const Group g{(int)threadIdx.x, (int)blockDim.x, 0};
     const FftPlan P = t.P;
-    const cx<T>* tw = tw_all + P.tw_off;
+    const TwTab<T> tw = load_twiddles(tws, tw_all + P.tw_off, P.L, g);
     if (g.tid < MAXOPS) ops_s[g.tid] = t.ops[g.tid];
     g.sync();
-    void* dbase = (t.dst_buf == BUF_WS) ? (void*)(ws + t.dst)
-                                        : (void*)((char*)out + t.dst * ((t.dst_real & 1) ? sizeof(T) : sizeof(cx<T>)));
     if (t.src_mode == SRC_OPERAND) {
         const bool real = t.dst_real & 2;  // bit 1 of dst_real flags a real input operand
         const void* sbase = (const char*)in + t.src * (real ? sizeof(T) : sizeof(cx<T>));
-        line_run<T>(P, OperandLoad<T>{sbase, t.src_len, t.src_stride, t.src_conj, real ? 1 : 0}, b0, b1,
-                    LineSink<T>{dbase, t.dst_len, t.dst_stride, t.dst_conj, t.dst_real & 1, (T)t.scale},
-                    t.inplace != 0, tw, g);
+        const OperandLoad<T> ld{sbase, t.src_len, t.src_stride, t.src_conj, real ? 1 : 0};
+        for (int i = g.tid; i < P.L; i += g.nthr) b0[sp(i)] = ld(i);
     } else {
-        line_run<T>(P, ProductLoad<T>{ws, ops_s, t.nops, t.along, t.fixed, t.Pp, t.Qp, t.src_len, t.src_conj,
-                                      t.rev_mask},
-                    b0, b1, LineSink<T>{dbase, t.dst_len, t.dst_stride, t.dst_conj, t.dst_real & 1, (T)t.scale},
-                    t.inplace != 0, tw, g);
+        const ProductLoad<T> ld{ws, ops_s, t.nops, t.along, t.fixed, t.Pp, t.Qp, t.src_len, t.src_conj, t.rev_mask};
+        for (int i = g.tid; i < P.L; i += g.nthr) b0[sp(i)] = ld(i);
     }
+    g.sync();
+    void* dbase = (t.dst_buf == BUF_WS) ? (void*)(ws + t.dst)
+                                        : (void*)((char*)out + t.dst * ((t.dst_real & 1) ? sizeof(T) : sizeof(cx<T>)));
+    fft_stage<T>(P, GLd<T>{nullptr, 0, nullptr, 0}, b0, b1, b0,
+                 LineSink<T>{dbase, t.dst_len, t.dst_stride, t.dst_conj, t.dst_real & 1, (T)t.scale}, false, tw, g);
 }
 
 template <typename T>
@@ -432,6 +427,21 @@ std::vector<Launch> merge(const std::vector<Launch>& in, const std::vector<int>&
     return out;
 }
 
+// Reorder the task table so that the tasks of consecutive launches of every
+// program are contiguous (launches of one phase can then be merged).
+void compact(std::vector<LineTask>& lines, std::vector<std::vector<Launch>*> progs) {
+    std::vector<LineTask> out;
+    out.reserve(lines.size());
+    for (auto* prog : progs)
+        for (auto& l : *prog) {
+            if (l.kind != 0) continue;
+            const int nf = (int)out.size();
+            out.insert(out.end(), lines.begin() + l.first, lines.begin() + l.first + l.count);
+            l.first = nf;
+        }
+    lines.swap(out);
+}
+
 hankel_status cuerr(cudaError_t e, const char* what, std::string& err) {
     err = std::string(what) + ": " + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? HANKEL_ENOMEM : HANKEL_ECUDA;
@@ -448,7 +458,9 @@ hankel_status upload(const std::vector<V>& v, V** d, std::string& err) {
     return HANKEL_OK;
 }
 
-size_t line_smem(const GeneralPlan* g, int L) { return RED_BYTES + 2 * smem_elems_host(L) * csize(g); }
+size_t line_smem(const GeneralPlan* g, int L) {
+    return RED_BYTES + ((size_t)TWG_SMEM + 2 * smem_elems_host(L)) * csize(g);
+}
 
 int nthr_for(int L) {
     int p = 1;
@@ -488,7 +500,7 @@ hankel_status general_create(GeneralPlan** out, const std::vector<hankel_desc>& 
     const size_t cs = csize(g);
     const int maxL = (int)std::min<int64_t>(16384, [&] {
         int L = 2;
-        while (L < 16384 && RED_BYTES + 2 * smem_elems_host(L + 1) * cs <= 227 * 1024) ++L;
+        while (L < 16384 && RED_BYTES + ((size_t)TWG_SMEM + 2 * smem_elems_host(L + 1)) * cs <= 227 * 1024) ++L;
         return (int64_t)L;
     }());
     std::map<std::tuple<int, int64_t, int, int, int, int>, int> opidx;
@@ -559,12 +571,16 @@ hankel_status general_create(GeneralPlan** out, const std::vector<hankel_desc>& 
     int64_t tw_total = 0;
     for (auto& kv : g->tw_off) {
         kv.second = (int)tw_total;
-        tw_total += kv.first;
+        tw_total += tw_table_elems(kv.first);
     }
     cudaError_t e = cudaMalloc(&g->d_tw, std::max<int64_t>(tw_total, 1) * cs);
     if (e != cudaSuccess) { delete g; return cuerr(e, "cudaMalloc(twiddles)", err); }
     for (auto& kv : g->tw_off) {
-        e = launch_twiddles(g->dbl, (char*)g->d_tw + (size_t)kv.second * cs, kv.first, 0);
+        if (kv.first < 2) continue;  // Q = 1: no transform along that axis
+        FftPlan TP;
+        std::memset(&TP, 0, sizeof(TP));
+        TP.L = kv.first;
+        e = launch_stage_twiddles(g->dbl, (char*)g->d_tw + (size_t)kv.second * cs, TP, 0);
         if (e != cudaSuccess) { general_destroy(g); return cuerr(e, "twiddle kernel", err); }
     }
     g->ws_bytes = (size_t)std::max<int64_t>(plane_cursor, 1) * cs;
@@ -607,6 +623,7 @@ hankel_status general_create(GeneralPlan** out, const std::vector<hankel_desc>& 
     prog.insert(prog.end(), pd1.begin(), pd1.end());
     cuts.push_back((int)prog.size());
     prog.insert(prog.end(), pd0.begin(), pd0.end());
+    compact(g->fwd_lines, {&prog});
     g->fwd_prog = merge(prog, cuts);
     (void)spec_end;
     for (size_t i = 0; i < g->ds.size(); ++i) {
@@ -623,7 +640,8 @@ hankel_status general_create(GeneralPlan** out, const std::vector<hankel_desc>& 
     }
 
     // ---- backward program: G planes, spectral sums, transforms to gradients
-    std::vector<Launch> bspec, bg0, bg1;
+    std::vector<Launch> bspec, bg0, bg1, spec_list;
+    std::vector<int> spec_cuts;
     for (size_t o = 0; o < g->ops.size(); ++o) emit_operand_spectrum(g, (int)o, g->bwd_lines, bspec);
     {
         std::vector<Launch> d0, d1;
@@ -631,7 +649,8 @@ hankel_status general_create(GeneralPlan** out, const std::vector<hankel_desc>& 
         std::vector<int> c2{(int)d0.size()};
         d0.insert(d0.end(), d1.begin(), d1.end());
         c2.push_back((int)d0.size());
-        g->bwd_prog_spec = merge(d0, c2);
+        spec_list = d0;
+        spec_cuts = c2;
     }
     // G_t = fft2(grad_y~): dim-0 over the N1 nonzero columns, then dim 1
     for (size_t i = 0; i < g->ds.size(); ++i) {
@@ -779,6 +798,8 @@ hankel_status general_create(GeneralPlan** out, const std::vector<hankel_desc>& 
         rest.insert(rest.end(), bt1.begin(), bt1.end());
         c3.push_back((int)rest.size());
         rest.insert(rest.end(), bt0.begin(), bt0.end());
+        compact(g->bwd_lines, {&spec_list, &rest});
+        g->bwd_prog_spec = merge(spec_list, spec_cuts);
         g->bwd_prog_rest = merge(rest, c3);
     }
     hankel_status s;

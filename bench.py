@@ -127,6 +127,26 @@ def read_clocks(path, proc, gpu_index):
             "samples": len(sm)}
 
 
+def rank_seed(rank):
+    """Each rank benchmarks its own batch (weak scaling): seed 1 + rank."""
+    return 1 + int(rank)
+
+
+def max_over_ranks(value, dist, device):
+    """Largest value over all ranks (a step time): the job's wall time."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(world, per_rank_units, seconds):
+    """Whole-job throughput: units processed by all ranks / slowest rank's time."""
+    return world * per_rank_units / seconds
+
+
 def profiled_traffic():
     """DRAM bytes per step of the forward kernel from the committed ncu
     capture, or None when the kernel sources changed since it was taken."""
@@ -297,7 +317,7 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
 
     # each rank processes its own full batch (weak scaling: fixed work per GPU)
-    batch = wl.batched_square(count=8192, seed=1 + rank)
+    batch = wl.batched_square(count=8192, seed=rank_seed(rank))
     descs = hk.batch_descs(batch)
     plan = hk.Plan(descs, hk.R32, hk.SAME_X)
     info = plan.info
@@ -334,12 +354,8 @@ def main():
     clocks = read_clocks(clk_path, sampler, local) if rank == 0 else None
     total_ms = t_start.elapsed_time(t_end)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = total_ms / args.steps
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * len(batch) / (ms / 1000.0)
+    ms = max_over_ranks(total_ms / args.steps, dist, dev)
+    value = aggregate_rate(world, len(batch), ms / 1000.0)
 
     # roofline of the forward kernel: algorithmic bytes per step / kernel time
     alg_bytes = float(sum(4 * (m * (n - 1) + 1 + 2 * n) for m, n in zip(batch.orders, batch.dims)))
@@ -359,12 +375,8 @@ def main():
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         plan.txv_host(hh, xh, yh, None, stream)
-    e2e_dt = (time.perf_counter() - t0) / e2e_steps
-    if dist:
-        t = torch.tensor([e2e_dt], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_dt = float(t.item())
-    e2e = {"value": world * len(batch) / e2e_dt, "unit": "products/s",
+    e2e_dt = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dist, dev)
+    e2e = {"value": aggregate_rate(world, len(batch), e2e_dt), "unit": "products/s",
            "h2d_bytes_per_step": int(hh.numel() * 4 + xh.numel() * 4), "d2h_bytes_per_step": int(yh.numel() * 4),
            "ms_per_step": 1000.0 * e2e_dt}
 

@@ -364,6 +364,32 @@ def main():
     achieved = alg_bytes / (kernel_ms / 1000.0) / 1e9
     traffic = profiled_traffic()
 
+    # the same step replayed from a CUDA graph (the launches and the plan's
+    # stream fork/join captured once)
+    graph = None
+    try:
+        gs = torch.cuda.Stream()
+        gs.wait_stream(stream)
+        torch.cuda.synchronize()
+        cg = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(cg, stream=gs):
+            plan.txv(Hs[0], Xs[0], Ys[0], None, gs)
+        for _ in range(3):
+            cg.replay()
+        torch.cuda.synchronize()
+        ga, gb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ga.record(stream)
+        for _ in range(args.steps):
+            cg.replay()
+        gb.record(stream)
+        torch.cuda.synchronize()
+        gms = max_over_ranks(ga.elapsed_time(gb) / args.steps, dist, dev)
+        graph = {"value": aggregate_rate(world, len(batch), gms / 1000.0), "unit": "products/s",
+                 "ms_per_step": gms, "note": "replays of one captured step on one input copy (L2-warm)"}
+        del cg
+    except Exception as exc:  # report, do not fail the benchmark
+        graph = {"error": str(exc)[:200]}
+
     # end to end through the host-buffer entry point
     hh = torch.tensor(batch.h, dtype=torch.float32).pin_memory()
     xh = torch.tensor(batch.x, dtype=torch.float32).pin_memory()
@@ -435,7 +461,7 @@ def main():
                              "algorithmic_bytes_per_step": alg_bytes},
                 "e2e": e2e, "gpu_launches": int(info["launches"]) * args.steps,
                 "plan": info, "fp64_plain": fp64, "cpu_baseline": cpu, "clocks": clocks,
-                "secondary": secondary,
+                "secondary": secondary, "graph_replay": graph,
                 "step_ms_min": float(np.min(step_ms)), "step_ms_median": float(np.median(step_ms))}
         print(json.dumps(line))
     plan.close()

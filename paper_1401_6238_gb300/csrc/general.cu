@@ -473,8 +473,17 @@ cudaError_t run_lines(GeneralPlan* g, const std::vector<Launch>& prog, const Lin
                       void* out, cudaStream_t st) {
     for (const Launch& l : prog) {
         const size_t smem = line_smem(g, l.L);
-        cudaError_t e = cudaFuncSetAttribute(line_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        // raise the limit only when needed (no attribute calls in steady state,
+        // so the launches can be captured into CUDA graphs); per device
+        static size_t granted[64] = {0};
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return e;
+        if (smem > granted[dev & 63]) {
+            e = cudaFuncSetAttribute(line_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            granted[dev & 63] = smem;
+        }
         line_kernel<T><<<l.count, nthr_for(l.L), smem, st>>>(d_tasks, l.first, in, out, (cx<T>*)g->d_ws,
                                                            (const cx<T>*)g->d_tw, l.L);
         e = cudaGetLastError();

@@ -355,6 +355,22 @@ __global__ void twiddle_kernel(cx<T>* out, int L) {
 
 // ------------------------------------------------------------------ host side
 
+// Raise a kernel's dynamic shared-memory limit only when a launch needs more
+// than already granted (no attribute calls in steady state, so launches can
+// be captured into CUDA graphs).
+template <class K>
+static cudaError_t ensure_smem(K kernel, size_t bytes) {
+    static size_t granted[64] = {0};  // per device, one table per kernel signature
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    size_t& g = granted[dev & 63];
+    if (bytes <= g) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) g = bytes;
+    return e;
+}
+
 template <typename T>
 static size_t real_smem_bytes(const RealLaunch& lc) {
     return RED_BYTES + ((size_t)TW_SMEM + (size_t)lc.arrays * smem_elems(lc.Lmax)) * sizeof(cx<T>);
@@ -370,7 +386,7 @@ static cudaError_t launch_fwd_t(const RealLaunch& lc, const RealJob* jobs, const
         return cudaGetLastError();
     }
     auto k = real_fwd_kernel<T>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem(k, smem);
     if (e != cudaSuccess) return e;
     k<<<lc.count, lc.nthr, smem, st>>>(jobs, lc.first, (const T*)h, (const T*)x, (T*)y, (T*)alpha,
                                        (const cx<T>*)tw, (cx<T>*)ws, lc.Lmax, flags);
@@ -389,7 +405,7 @@ static cudaError_t launch_bwd_t(const RealLaunch& lc, const RealJob* jobs, const
         return cudaGetLastError();
     }
     auto k = real_bwd_kernel<T>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem(k, smem);
     if (e != cudaSuccess) return e;
     k<<<lc.count, lc.nthr, smem, st>>>(jobs, lc.first, (const T*)gy, (const T*)h, (const T*)x, (T*)gh, (T*)gx,
                                        (const cx<T>*)tw, (cx<T>*)ws, lc.Lmax, flags, stored);

@@ -240,6 +240,24 @@ hankel_status hankel_txv_backward_static(const hankel_desc* descs, int64_t count
 /* hankel_plan_query -- copy the plan's facts into *info. */
 hankel_status hankel_plan_query(hankel_plan_t plan, hankel_plan_info* info);
 
+/*
+ * hankel_set_tuning -- planner knobs for plans made after the call
+ * (process-wide; existing plans keep their choices).
+ *   pass_cost          fixed cost of one radix pass in the planner's cost
+ *                      model (FP32 operations per point, default 10): larger
+ *                      values favour FFT lengths with fewer passes.
+ *   points_per_thread  transform points each thread owns, 8, 16 (default),
+ *                      32 or 64: sets the threads per job.
+ * The project's autotuner (paper_1401_6238_gb300/autotune.py) times
+ * candidate settings on the device and caches the fastest in a JSON file
+ * that the Python binding applies when it loads the library.
+ * Errors: EINVAL for values outside the ranges above.
+ */
+hankel_status hankel_set_tuning(double pass_cost, int points_per_thread);
+
+/* hankel_get_tuning -- the current planner knobs. */
+hankel_status hankel_get_tuning(double* pass_cost, int* points_per_thread);
+
 /* hankel_fft_length -- the FFT length the planner picks for generating
  * length d (d >= 1), or -1 when d is beyond the supported maximum. */
 int64_t hankel_fft_length(int64_t d);

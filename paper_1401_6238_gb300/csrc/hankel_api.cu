@@ -7,6 +7,8 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -43,14 +45,11 @@ size_t elem_size(hankel_dtype d) { return real_size(d) * (is_complex(d) ? 2 : 1)
 // Radix set of the kernels and a per-point cost model of one Stockham pass
 // (shared-memory round trip + butterfly arithmetic, FP32 operations / point).
 constexpr int kMaxL = 16384;
-constexpr double kPassCost = 10.0;
-#ifndef HK_MAX16
-#define HK_MAX16 64
-#endif
-constexpr int kMax16 = HK_MAX16;  // radix-16 passes allowed per length
-#ifndef HK_THREAD_DIV
-#define HK_THREAD_DIV 16
-#endif
+// Planner knobs (hankel_set_tuning): the fixed cost of one pass in the
+// length/radix cost model, and the points each thread owns (threads per job).
+double g_pass_cost = 10.0;
+int g_points_per_thread = 16;
+std::mutex g_tune_mu;
 double radix_cost(int r) {
     switch (r) {
         case 2: return 5.0;
@@ -82,7 +81,7 @@ bool factor(int L, std::vector<int>& out, double& cost) {
     // split a into parts of size 4,3,2,1 (log2 of 16,8,4,2)
     double best = 1e18;
     std::vector<int> bestp;
-    for (int n4 = 0; n4 * 4 <= a && n4 <= kMax16; ++n4)
+    for (int n4 = 0; n4 * 4 <= a; ++n4)
         for (int n3 = 0; n4 * 4 + n3 * 3 <= a; ++n3)
             for (int n2 = 0; n4 * 4 + n3 * 3 + n2 * 2 <= a; ++n2) {
                 int n1 = a - n4 * 4 - n3 * 3 - n2 * 2;
@@ -92,14 +91,14 @@ bool factor(int L, std::vector<int>& out, double& cost) {
                 p.insert(p.end(), n2, 4);
                 p.insert(p.end(), n1, 2);
                 double c = 0;
-                for (int r : p) c += kPassCost + radix_cost(r);
+                for (int r : p) c += g_pass_cost + radix_cost(r);
                 if (c < best || (c == best && p.size() < bestp.size())) { best = c; bestp = p; }
             }
     out = bestp;
     out.insert(out.end(), odd.begin(), odd.end());
     std::sort(out.begin(), out.end(), [](int x, int y) { return x > y; });
     cost = 0;
-    for (int r : out) cost += kPassCost + radix_cost(r);
+    for (int r : out) cost += g_pass_cost + radix_cost(r);
     cost *= L;
     return !out.empty() && out.size() <= 8;
 }
@@ -134,9 +133,12 @@ struct LengthTable {
     }
 };
 
+// The table for the current knobs; rebuilt when hankel_set_tuning changes them.
+std::unique_ptr<LengthTable> g_lengths;
 const LengthTable& lengths() {
-    static LengthTable t;
-    return t;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (!g_lengths) g_lengths.reset(new LengthTable);
+    return *g_lengths;
 }
 
 int pow2ceil(int v) {
@@ -256,7 +258,10 @@ hankel_status upload_twiddles(hankel_plan_s* p, const std::vector<int>& Ls) {
 
 // Threads per block for a transform of length L: about one radix-16
 // butterfly per thread and pass, between one warp and 512 threads.
-int nthr_of(int L) { return std::max(32, std::min(512, pow2ceil((L + HK_THREAD_DIV - 1) / HK_THREAD_DIV))); }
+int nthr_of(int L) {
+    const int ppt = g_points_per_thread;
+    return std::max(32, std::min(512, pow2ceil((L + ppt - 1) / ppt)));
+}
 
 // Largest L whose `buffers` ping-pong arrays fit in one block's shared memory.
 constexpr size_t kSmemLimit = 227 * 1024;
@@ -588,6 +593,26 @@ hankel_status hankel_plan_query(hankel_plan_t p, hankel_plan_info* info) {
     } else {
         hk::general_info(p->gen, &info->jobs, &info->launches, &info->distinct_lengths, &info->workspace_bytes);
     }
+    return HANKEL_OK;
+}
+
+hankel_status hankel_set_tuning(double pass_cost, int points_per_thread) {
+    if (!(pass_cost >= 0.0 && pass_cost <= 1000.0))
+        return fail(HANKEL_EINVAL, "pass_cost %g outside [0, 1000]", pass_cost);
+    if (points_per_thread != 8 && points_per_thread != 16 && points_per_thread != 32 && points_per_thread != 64)
+        return fail(HANKEL_EINVAL, "points_per_thread %d is not 8, 16, 32 or 64", points_per_thread);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_pass_cost = pass_cost;
+    g_points_per_thread = points_per_thread;
+    g_lengths.reset();  // rebuilt with the new cost model on next use
+    return HANKEL_OK;
+}
+
+hankel_status hankel_get_tuning(double* pass_cost, int* points_per_thread) {
+    if (!pass_cost || !points_per_thread) return fail(HANKEL_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    *pass_cost = g_pass_cost;
+    *points_per_thread = g_points_per_thread;
     return HANKEL_OK;
 }
 

@@ -62,6 +62,8 @@ _SIGS = {
                                    [ctypes.c_void_p] * 6),
     "hankel_plan_query": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(PlanInfo)]),
     "hankel_fft_length": (ctypes.c_int64, [ctypes.c_int64]),
+    "hankel_set_tuning": (ctypes.c_int, [ctypes.c_double, ctypes.c_int]),
+    "hankel_get_tuning": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
     "hankel_plan_destroy": (None, [ctypes.c_void_p]),
     "hankel_last_error": (ctypes.c_char_p, []),
     "hankel_version": (ctypes.c_char_p, []),
@@ -84,7 +86,26 @@ def load():
             fn.restype = res
             fn.argtypes = args
         _lib = lib
+        _apply_cached_tuning()
     return _lib
+
+
+TUNING_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "autotune.json")
+
+
+def _apply_cached_tuning():
+    """Apply the autotuner's cached choice for this device, if there is one."""
+    try:
+        import json
+        import torch
+        if not os.path.exists(TUNING_PATH) or not torch.cuda.is_available():
+            return
+        rec = json.load(open(TUNING_PATH))
+        if rec.get("device") == torch.cuda.get_device_name():
+            best = rec["best"]
+            _lib.hankel_set_tuning(float(best["pass_cost"]), int(best["points_per_thread"]))
+    except Exception:
+        pass
 
 
 def _check(status):
@@ -158,6 +179,16 @@ def hankel_plan_query(plan):
 
 def hankel_fft_length(d):
     return int(load().hankel_fft_length(int(d)))
+
+
+def hankel_set_tuning(pass_cost, points_per_thread):
+    _check(load().hankel_set_tuning(float(pass_cost), int(points_per_thread)))
+
+
+def hankel_get_tuning():
+    c, p = ctypes.c_double(), ctypes.c_int()
+    _check(load().hankel_get_tuning(ctypes.byref(c), ctypes.byref(p)))
+    return c.value, p.value
 
 
 def hankel_plan_destroy(plan):

@@ -106,3 +106,24 @@ def test_null_plan_calls_return_einval(lib):
         assert fn(*args) == hk.EINVAL
     assert "NULL" in hk.hankel_last_error()
     lib.hankel_plan_destroy(None)  # ignored
+
+
+def test_tuning_knobs(lib):
+    old = hk.hankel_get_tuning()
+    try:
+        hk.hankel_set_tuning(0.0, 32)
+        assert hk.hankel_get_tuning() == (0.0, 32)
+        cheap = [hk.hankel_fft_length(d) for d in range(2000, 4100, 37)]
+        hk.hankel_set_tuning(500.0, 16)
+        costly = [hk.hankel_fft_length(d) for d in range(2000, 4100, 37)]
+        # the cost model changes the choice, and every choice stays a valid length
+        ds = list(range(2000, 4100, 37))
+        assert cheap != costly
+        assert all(L >= d and smooth(L) for d, L in zip(ds, cheap + costly[:0]))
+        assert all(L >= d and smooth(L) for d, L in zip(ds, costly))
+        for bad in [(-1.0, 16), (10.0, 12), (2000.0, 16)]:
+            with pytest.raises(hk.HankelError) as e:
+                hk.hankel_set_tuning(*bad)
+            assert e.value.status == hk.EINVAL
+    finally:
+        hk.hankel_set_tuning(*old)

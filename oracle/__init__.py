@@ -20,6 +20,8 @@ Contents (each function cites the passage it restates):
   Section 3 via 2D FFTs.
 * ``grad``    -- gradients of the products (the paper is silent on them; they
   are derived from the definition, see the module header).
+* ``edf``     -- HOOI / HOTF (Algorithms 4.1, 4.2) on explicit tensors and the
+  total-least-squares pole estimates of Sections 4.1 and 4.3.
 
 Parity status: every function here is pinned by ``tests/test_oracle*.py``
 against something other than itself (loops over index tuples, closed forms,
@@ -50,6 +52,7 @@ from .block import (
     fast_block_y,
     fast_block_alpha,
 )
+from . import edf  # noqa: F401
 from .grad import (
     brute_grads,
     fast_grads,

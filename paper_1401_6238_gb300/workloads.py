@@ -17,6 +17,8 @@ products and its Section 4 exponential-data-fitting signals):
 * ``grad_case``      -- m=4, n=4096 batch for the gradient checks.
 * ``edf_1d_signal`` / ``edf_2d_signal`` -- sums of damped complex
   exponentials plus complex Gaussian noise at a given SNR (Sections 4.1, 4.3).
+* ``damped_1d`` / ``damped_2d`` -- noiseless (or lightly noisy) damped
+  exponentials with given poles, e.g. the 2-peak signal of Example 4.1.
 * ``unit_columns``   -- random complex unit-norm columns standing in for the
   HOOI factor columns of Section 4.2.
 """
@@ -149,9 +151,10 @@ def _noise(rng, shape, signal, snr_db):
     return np.sqrt(p_noise / 2.0) * (rng.standard_normal(shape) + 1j * rng.standard_normal(shape))
 
 
-def edf_1d_signal(N=4094, K=8, snr_db=20.0, seed=4):
+def edf_1d_signal(N=4094, K=8, snr_db=20.0, seed=4, with_poles=False):
     """s_t = sum_k a_k e^{i phi_k} exp((-alpha_k + i omega_k) t) + noise
-    (the model of Section 4.1 with unit sampling interval)."""
+    (the model of Section 4.1 with unit sampling interval); with
+    ``with_poles`` also the true poles exp(-alpha_k + i omega_k)."""
     rng = np.random.default_rng(seed)
     alpha = rng.uniform(0.001, 0.05, K)
     omega = rng.uniform(-np.pi, np.pi, K)
@@ -161,7 +164,10 @@ def edf_1d_signal(N=4094, K=8, snr_db=20.0, seed=4):
     s = np.zeros(N, dtype=np.complex128)
     for k in range(K):
         s += amp[k] * np.exp(1j * phase[k]) * np.exp((-alpha[k] + 1j * omega[k]) * t)
-    return s + _noise(rng, N, s, snr_db)
+    noisy = s + _noise(rng, N, s, snr_db)
+    if with_poles:
+        return noisy, np.exp(-alpha + 1j * omega)
+    return noisy
 
 
 def edf_2d_signal(N1=256, N2=256, K=12, snr_db=20.0, seed=5):
@@ -178,6 +184,34 @@ def edf_2d_signal(N1=256, N2=256, K=12, snr_db=20.0, seed=5):
     for k in range(K):
         s += c[k] * np.exp((-a1[k] + 1j * w1[k]) * n1) * np.exp((-a2[k] + 1j * w2[k]) * n2)
     return s + _noise(rng, (N1, N2), s, snr_db)
+
+
+def damped_2d(N1, N2, peaks, noise_std=0.0, seed=8):
+    """x_{n1 n2} = sum_k exp((a_k + 2 pi i f_k) n1) exp((b_k + 2 pi i g_k) n2)
+    plus complex Gaussian noise of the given standard deviation; ``peaks`` is
+    a list of (a_k, f_k, b_k, g_k) (the 2-peak signal of Section 4.3,
+    Example 4.1, takes its parameters from the paper)."""
+    n1 = np.arange(N1)[:, None]
+    n2 = np.arange(N2)[None, :]
+    x = np.zeros((N1, N2), dtype=np.complex128)
+    for a, f, b, g in peaks:
+        x += np.exp((a + 2j * np.pi * f) * n1) * np.exp((b + 2j * np.pi * g) * n2)
+    if noise_std > 0:
+        rng = np.random.default_rng(seed)
+        x += noise_std * (rng.standard_normal(x.shape) + 1j * rng.standard_normal(x.shape)) / np.sqrt(2)
+    return x
+
+
+def damped_1d(N, poles, amps, noise_std=0.0, seed=9):
+    """x_n = sum_k c_k z_k^n plus complex Gaussian noise (Section 4.1)."""
+    n = np.arange(N)
+    x = np.zeros(N, dtype=np.complex128)
+    for z, c in zip(poles, amps):
+        x += c * np.asarray(z, dtype=np.complex128) ** n
+    if noise_std > 0:
+        rng = np.random.default_rng(seed)
+        x += noise_std * (rng.standard_normal(N) + 1j * rng.standard_normal(N)) / np.sqrt(2)
+    return x
 
 
 def unit_columns(n, R, seed=6):

@@ -1,0 +1,90 @@
+"""Pins for the oracle's exponential-data-fitting layer (Section 4) on CPU:
+the rank statements of Section 4.3, the printed poles of Example 4.1, exact
+recovery of 1D poles from a noiseless signal, TLS on consistent systems, and
+the monotone core norm of HOOI."""
+
+import numpy as np
+import pytest
+from scipy.optimize import linear_sum_assignment
+
+import oracle
+from conftest import golden
+from oracle import edf
+from paper_1401_6238_gb300 import workloads as wl
+
+
+def match(est, true):
+    est, true = np.asarray(est), np.asarray(true)
+    C = np.abs(est[:, None] - true[None, :])
+    r, c = linear_sum_assignment(C)
+    return C[r, c].max()
+
+
+def example41():
+    g = golden("example41_poles.txt")
+    z = {(int(d), int(k)): np.exp(a + 2j * np.pi * f) for d, k, a, f in g}
+    peaks = [(g[0, 2], g[0, 3], g[2, 2], g[2, 3]), (g[1, 2], g[1, 3], g[3, 2], g[3, 3])]
+    return z, peaks
+
+
+def test_tls_solves_consistent_systems():
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((20, 3)) + 1j * rng.standard_normal((20, 3))
+    W0 = rng.standard_normal((3, 3)) + 1j * rng.standard_normal((3, 3))
+    np.testing.assert_allclose(edf.tls(A, A @ W0), W0, atol=1e-10)
+
+
+def test_1d_noiseless_rank_and_exact_poles():
+    # x_n = sum_k c_k z_k^n, K = 3: the 8 x 8 x 8 Hankel tensor (N = 22) has
+    # exactly K nonzero mode singular values and the poles come back exactly
+    poles = [0.95 * np.exp(0.4j), 0.9 * np.exp(-1.1j), 0.98 * np.exp(2.0j)]
+    x = wl.damped_1d(22, poles, [1.0, 0.7 - 0.2j, 1.3j])
+    A = oracle.hankel_tensor(x, [8, 8, 8])
+    s = np.linalg.svd(edf.unfold(A, 1), compute_uv=False)
+    assert s[3] < 1e-12 * s[0] and s[2] > 1e-3 * s[0]
+    U, S, sv = edf.hotf(A, 3, sweeps=2)
+    assert match(edf.poles_1d(U, 3), poles) < 1e-9
+    Us, S2, _ = edf.hooi(A, 3, sweeps=2)
+    assert match(edf.poles_1d(Us[0], 3), poles) < 1e-9
+
+
+def test_example_41_rank_two_mode_singular_values():
+    # Section 4.3: the BHHB tensor of size 6x6x6 with blocks 3x3x3 built from
+    # the noiseless 2-peak signal has only two nonzero mode-1 singular values
+    z, peaks = example41()
+    I, J = 3, 2
+    X = wl.damped_2d(3 * I - 2, 3 * J - 2, peaks)
+    T = oracle.bhhb_tensor(X, [I] * 3, [J] * 3)
+    assert T.shape == (6, 6, 6)
+    s = np.linalg.svd(edf.unfold(T, 1), compute_uv=False)
+    assert s[1] > 1e-3 * s[0] and np.all(s[2:] < 1e-12 * s[0])
+
+
+def test_example_41_poles_from_hotf_and_two_tls():
+    # Section 4.3: HOTF of the rank-(2,2,2) approximation of the 30x30x30 BHHB
+    # tensor with 6x6x6 blocks, then TLS twice, gives the printed poles
+    z, peaks = example41()
+    I, J = 6, 5
+    X = wl.damped_2d(3 * I - 2, 3 * J - 2, peaks)
+    T = oracle.bhhb_tensor(X, [I] * 3, [J] * 3)
+    assert T.shape == (30, 30, 30)
+    U, S, _ = edf.hotf(T, 2, sweeps=2)
+    z1, z2 = edf.poles_2d(U, I, J, 2)
+    assert match(z1, [z[(1, 1)], z[(1, 2)]]) < 1e-9
+    assert match(z2, [z[(2, 1)], z[(2, 2)]]) < 1e-9
+    # pairing: peak k has (z1, z2) = (z[(1,k)], z[(2,k)])
+    pairs = sorted(zip(np.round(z1, 8), np.round(z2, 8)), key=lambda t: t[0].imag)
+    want = sorted([(z[(1, 1)], z[(2, 1)]), (z[(1, 2)], z[(2, 2)])], key=lambda t: t[0].imag)
+    for (a, b), (c, d) in zip(pairs, want):
+        assert abs(a - c) < 1e-7 and abs(b - d) < 1e-7
+
+
+def test_hooi_core_norm_does_not_decrease():
+    rng = np.random.default_rng(1)
+    A = rng.standard_normal((7, 6, 5)) + 1j * rng.standard_normal((7, 6, 5))
+    Us = edf.hosvd_init(A, 2)
+    norms = []
+    for _ in range(5):
+        Us, S, _ = edf.hooi(A, 2, sweeps=1, Us=Us)
+        norms.append(np.linalg.norm(S))
+    assert all(b >= a - 1e-12 for a, b in zip(norms, norms[1:]))

@@ -14,6 +14,10 @@ across blocks (index j, poles z_2).
 Everything here works on the explicit (dense) tensor with numpy's SVD, so
 only small sizes are practical:
 
+* ``reduced_unfolding``    -- Section 4.2: the mode-p unfolding of a Hankel
+  tensor with its repeated columns removed, the I_p x (d - I_p + 1) Hankel
+  matrix of the same generating vector (and its two-level analogue for a
+  BHHB tensor); the initial factors are its leading left singular vectors.
 * ``hosvd_init`` / ``hooi``  -- Algorithm 4.1 (HOOI): U_p from the HOSVD,
   then repeatedly U_p <- R leading left singular vectors of
   Unfold_p(A x_q conj(U_q) for q != p); core S = A x_1 conj(U_1) ... .
@@ -41,6 +45,28 @@ def leading_left(M, R):
     """R leading left singular vectors and all singular values of M."""
     U, s, _ = np.linalg.svd(M, full_matrices=False)
     return U[:, :R], s
+
+
+def reduced_unfolding(h, dims, p):
+    """Section 4.2: M[i, a] = h[i + a], i < I_p, a <= d - I_p (p 1-based)."""
+    h = np.asarray(h)
+    I = dims[p - 1]
+    return np.array([[h[i + a] for a in range(len(h) - I + 1)] for i in range(I)])
+
+
+def reduced_block_unfolding(G, n, N, p):
+    """Two-level analogue for a BHHB tensor with generating matrix G: rows
+    i + n_p j, columns a + (rows(G) - n_p + 1) b, entry G[i + a, j + b]."""
+    G = np.asarray(G)
+    n_p, N_p = n[p - 1], N[p - 1]
+    A, B = G.shape[0] - n_p + 1, G.shape[1] - N_p + 1
+    M = np.zeros((n_p * N_p, A * B), dtype=G.dtype)
+    for j in range(N_p):
+        for i in range(n_p):
+            for b in range(B):
+                for a in range(A):
+                    M[i + n_p * j, a + A * b] = G[i + a, j + b]
+    return M
 
 
 def hosvd_init(A, R):

@@ -170,8 +170,9 @@ def edf_1d_signal(N=4094, K=8, snr_db=20.0, seed=4, with_poles=False):
     return noisy
 
 
-def edf_2d_signal(N1=256, N2=256, K=12, snr_db=20.0, seed=5):
-    """x_{n1 n2} = sum_k c_k z_{1,k}^{n1} z_{2,k}^{n2} + noise (Section 4.3)."""
+def edf_2d_signal(N1=256, N2=256, K=12, snr_db=20.0, seed=5, with_poles=False):
+    """x_{n1 n2} = sum_k c_k z_{1,k}^{n1} z_{2,k}^{n2} + noise (Section 4.3);
+    with ``with_poles`` also the true pole pairs (z_1, z_2)."""
     rng = np.random.default_rng(seed)
     a1 = rng.uniform(0.002, 0.03, K)
     a2 = rng.uniform(0.002, 0.03, K)
@@ -183,7 +184,10 @@ def edf_2d_signal(N1=256, N2=256, K=12, snr_db=20.0, seed=5):
     s = np.zeros((N1, N2), dtype=np.complex128)
     for k in range(K):
         s += c[k] * np.exp((-a1[k] + 1j * w1[k]) * n1) * np.exp((-a2[k] + 1j * w2[k]) * n2)
-    return s + _noise(rng, (N1, N2), s, snr_db)
+    noisy = s + _noise(rng, (N1, N2), s, snr_db)
+    if with_poles:
+        return noisy, (np.exp(-a1 + 1j * w1), np.exp(-a2 + 1j * w2))
+    return noisy
 
 
 def damped_2d(N1, N2, peaks, noise_std=0.0, seed=8):

@@ -88,3 +88,32 @@ def test_hooi_core_norm_does_not_decrease():
         Us, S, _ = edf.hooi(A, 2, sweeps=1, Us=Us)
         norms.append(np.linalg.norm(S))
     assert all(b >= a - 1e-12 for a, b in zip(norms, norms[1:]))
+
+
+def _column_set(M):
+    return {tuple(np.round(c, 12)) for c in M.T}
+
+
+@pytest.mark.parametrize("dims,p", [([5, 4, 3], 1), ([5, 4, 3], 2), ([4, 4, 4, 2], 4)])
+def test_reduced_unfolding_holds_exactly_the_distinct_columns(dims, p):
+    # Section 4.2: removing repeated columns of the mode-p unfolding leaves
+    # the Hankel matrix of the same generating vector
+    rng = np.random.default_rng(p)
+    h = rng.standard_normal(sum(dims) - len(dims) + 1) + 1j * rng.standard_normal(sum(dims) - len(dims) + 1)
+    full = edf.unfold(oracle.hankel_tensor(h, dims), p)
+    red = edf.reduced_unfolding(h, dims, p)
+    assert red.shape == (dims[p - 1], len(h) - dims[p - 1] + 1)
+    assert _column_set(full) == _column_set(red)
+    assert len(_column_set(red)) == red.shape[1]
+
+
+def test_reduced_block_unfolding_holds_exactly_the_distinct_columns():
+    rng = np.random.default_rng(3)
+    n, N = [3, 2, 2], [2, 3, 2]
+    G = rng.standard_normal((5, 5)) + 1j * rng.standard_normal((5, 5))
+    T = oracle.bhhb_tensor(G, n, N)
+    for p in (1, 2, 3):
+        full = edf.unfold(T, p)
+        red = edf.reduced_block_unfolding(G, n, N, p)
+        assert red.shape == (n[p - 1] * N[p - 1], (6 - n[p - 1]) * (6 - N[p - 1]))
+        assert _column_set(full) == _column_set(red)

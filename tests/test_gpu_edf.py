@@ -169,6 +169,48 @@ def test_example_41_rank_two(edf):
     h.close()
 
 
+@pytest.mark.parametrize("sigma", [0.0, 1e-4, 1e-2])
+def test_example_41_mode1_singular_values(edf, sigma):
+    # Section 4.3, Example 4.1: the mode-1 singular values of the 6x6x6 BHHB
+    # tensor (3x3x3 blocks).  With R = 6 the factor is unitary, so one HOTF
+    # update's unfolding has exactly the tensor's mode-1 singular values.
+    z, peaks = example41()
+    X = wl.damped_2d(7, 4, peaks, noise_std=sigma, seed=0)
+    want = np.linalg.svd(oedf.unfold(oracle.bhhb_tensor(X, [3] * 3, [2] * 3), 1), compute_uv=False)
+    T = edf.HankelTensor(X, [3] * 3, [2] * 3, dtype=hk.C128)
+    h = edf.HOOI(T, 6, symmetric=True).init()
+    s = np_(h.update(0))
+    assert np.abs(s - want).max() < 1e-12 * want[0]
+    if sigma == 0:
+        assert s[1] > 0.5 * s[0] and s[2] < 1e-12 * s[0]
+    h.close()
+
+
+@pytest.mark.parametrize("sigma", [1e-6, 1e-3])
+def test_example_41_noisy_poles_match_oracle(edf, sigma):
+    # Example 4.1 with noise: from the same start, the GPU HOTF + TLS gives
+    # the oracle's pole estimates, and their error is at the noise level
+    z, peaks = example41()
+    X = wl.damped_2d(16, 13, peaks, noise_std=sigma, seed=1)
+    A = oracle.bhhb_tensor(X, [6] * 3, [5] * 3)
+    U0 = oedf.leading_left(oedf.unfold(A, 1), 2)[0]
+    Uo, _, _ = oedf.hotf(A, 2, 3, U=U0)
+    ao, bo = oedf.poles_2d(Uo, 6, 5, 2)
+    T = edf.HankelTensor(X, [6] * 3, [5] * 3, dtype=hk.C128)
+    h = edf.HOOI(T, 2, symmetric=True)
+    h.set_factor(0, torch.tensor(U0))
+    h.fit(3)
+    a, b = edf.poles_2d(h.U[0], 6, 5, 2)
+    a, b = np_(a), np_(b)
+    e, r, c = match(a, ao)
+    assert e < 1e-10
+    assert np.abs(b[r] - bo[c]).max() < 1e-10
+    want = {1: (z[(1, 1)], z[(2, 1)]), 2: (z[(1, 2)], z[(2, 2)])}
+    err = max(max(abs(x - w[0]) / abs(w[0]), abs(y - w[1]) / abs(w[1]))
+              for x, y in zip(a, b) for w in [min(want.values(), key=lambda w: abs(w[0] - x))])
+    assert 1e-3 * sigma < err < sigma
+
+
 def test_1d_full_size_hooi(edf):
     # 1D signal of length 4094, K = 8, 20 dB: order-3 Hankel 1366x1365x1365,
     # Algorithm 4.1 with R = 8, complex64

@@ -117,3 +117,32 @@ def test_reduced_block_unfolding_holds_exactly_the_distinct_columns():
         red = edf.reduced_block_unfolding(G, n, N, p)
         assert red.shape == (n[p - 1] * N[p - 1], (6 - n[p - 1]) * (6 - N[p - 1]))
         assert _column_set(full) == _column_set(red)
+
+
+def _rel_pole_error(z1, z2, z):
+    """Largest relative error of the estimated (z_1, z_2) pairs against the
+    exact pairs of Example 4.1, pairs matched on z_1."""
+    want = [(z[(1, 1)], z[(2, 1)]), (z[(1, 2)], z[(2, 2)])]
+    err = 0.0
+    for a, b in zip(z1, z2):
+        t1, t2 = min(want, key=lambda w: abs(w[0] - a))
+        err = max(err, abs(a - t1) / abs(t1), abs(b - t2) / abs(t2))
+    return err
+
+
+def test_example_41_error_tracks_the_noise():
+    # Section 4.3, Example 4.1: with noise, the relative pole errors of the
+    # 30x30x30 HOTF + TLS estimate are at the level of the noise, and the
+    # mode-1 singular values of the 6x6x6 tensor beyond the second are too
+    z, peaks = example41()
+    ratios = []
+    for sigma in (1e-6, 1e-4, 1e-2):
+        for seed in range(3):
+            X = wl.damped_2d(16, 13, peaks, noise_std=sigma, seed=seed)
+            U, _, _ = edf.hotf(oracle.bhhb_tensor(X, [6] * 3, [5] * 3), 2, sweeps=3)
+            ratios.append(_rel_pole_error(*edf.poles_2d(U, 6, 5, 2), z) / sigma)
+        X = wl.damped_2d(7, 4, peaks, noise_std=sigma, seed=0)
+        s = np.linalg.svd(edf.unfold(oracle.bhhb_tensor(X, [3] * 3, [2] * 3), 1), compute_uv=False)
+        assert s[1] > 0.5 * s[0] and 0.1 * sigma < s[2] / s[0] < 10 * sigma
+    assert max(ratios) < 1.0 and min(ratios) > 1e-3
+    assert max(ratios) / min(ratios) < 5.0  # linear in the noise level

@@ -20,6 +20,8 @@ Contents (each function cites the passage it restates):
   Section 3 via 2D FFTs.
 * ``grad``    -- gradients of the products (the paper is silent on them; they
   are derived from the definition, see the module header).
+* ``level``   -- level-k block Hankel tensors (Section 2.2) and their fast
+  products by k-dimensional FFTs (end of Section 3), with gradients.
 * ``edf``     -- HOOI / HOTF (Algorithms 4.1, 4.2) on explicit tensors and the
   total-least-squares pole estimates of Sections 4.1 and 4.3.
 
@@ -28,7 +30,7 @@ against something other than itself (loops over index tuples, closed forms,
 library routines, finite differences, printed examples).
 """
 
-from .fft import fft, ifft, fft2, ifft2, next_pow2
+from .fft import fft, ifft, fft2, ifft2, fftn, ifftn, next_pow2
 from .hankel import (
     d_of,
     hankel_tensor,
@@ -53,6 +55,7 @@ from .block import (
     fast_block_alpha,
 )
 from . import edf  # noqa: F401
+from . import level  # noqa: F401
 from .grad import (
     brute_grads,
     fast_grads,
@@ -61,7 +64,7 @@ from .grad import (
 )
 
 __all__ = [
-    "fft", "ifft", "fft2", "ifft2", "next_pow2",
+    "fft", "ifft", "fft2", "ifft2", "fftn", "ifftn", "next_pow2",
     "d_of", "hankel_tensor", "mode_product", "loop_y", "loop_alpha",
     "brute_y", "brute_alpha", "fast_y", "fast_alpha",
     "anticirculant_generating_vector", "anticirculant_y", "anticirculant_alpha",

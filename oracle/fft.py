@@ -68,3 +68,19 @@ def fft2(A):
 def ifft2(A):
     """2D inverse DFT ``conj(F_P) A conj(F_Q) / (P Q)``."""
     return ifft(ifft(A, axis=0), axis=1)
+
+
+def fftn(A):
+    """k-dimensional DFT: ``fft`` along every axis in turn."""
+    A = np.asarray(A, dtype=np.complex128)
+    for ax in range(A.ndim):
+        A = fft(A, axis=ax)
+    return A
+
+
+def ifftn(A):
+    """k-dimensional inverse DFT: ``ifft`` along every axis in turn."""
+    A = np.asarray(A, dtype=np.complex128)
+    for ax in range(A.ndim):
+        A = ifft(A, axis=ax)
+    return A

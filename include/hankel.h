@@ -109,6 +109,34 @@ typedef struct hankel_desc {
     int64_t y_off;
 } hankel_desc;
 
+/*
+ * One level-k block Hankel tensor (Section 2.2: a block Hankel tensor whose
+ * blocks are level-(k-1) block Hankel tensors; level 1 is a Hankel tensor,
+ * level 2 a BHHB tensor).
+ *   m       order, 2 <= m <= HANKEL_MAX_ORDER.
+ *   levels  k, 1 <= k <= HANKEL_MAX_LEVELS.
+ *   n[l][p] size of mode p+1 at level l+1 (level 1 innermost).  Mode p+1
+ *           has prod_l n[l][p] entries; its index in mixed radix, level 1
+ *           fastest, is I = a_1 + n[0][p] (a_2 + n[1][p] (a_3 + ...)), and
+ *           the tensor entry is G[sum_p a_1, ..., sum_p a_k].
+ *   h_off   offset of the generating tensor G, an order-k array of size
+ *           D_l = sum_p n[l][p] - m + 1 along level l, stored column-major
+ *           (level 1 fastest).
+ *   x_off   offsets of x_1..x_m: x_p is an array of size n[0][p] x ... x
+ *           n[k-1][p], column-major (only x_off[0] with HANKEL_SAME_X).
+ *   y_off   offset of y, laid out like x_1.
+ * A level whose sizes are all 1 adds nothing (its D_l is 1).
+ */
+#define HANKEL_MAX_LEVELS 4
+typedef struct hankel_mdesc {
+    int32_t m;
+    int32_t levels;
+    int32_t n[HANKEL_MAX_LEVELS][HANKEL_MAX_ORDER];
+    int64_t h_off;
+    int64_t x_off[HANKEL_MAX_ORDER];
+    int64_t y_off;
+} hankel_mdesc;
+
 typedef struct hankel_plan_s* hankel_plan_t;
 typedef struct CUstream_st* hankel_stream_t; /* same type as cudaStream_t */
 
@@ -144,6 +172,25 @@ hankel_status hankel_plan(hankel_plan_t* out, const hankel_desc* descs, int64_t 
                           hankel_dtype dtype, uint32_t flags);
 
 /*
+ * hankel_plan_multilevel -- a plan for level-k block Hankel tensors
+ * (Section 2.2; the fast products of Section 3 with k-dimensional FFTs, as
+ * the end of Section 3 states):
+ *   Y = fftn(ifftn(G~) .* fftn(X~_2) .* ... .* fftn(X~_m))[0:n[0][0], ..., 0:n[k-1][0]],
+ *   alpha = <ifftn(G~), fftn(X~_1) .* ... .* fftn(X~_m)>,
+ * every array zero-padded to L_1 x ... x L_k with L_l >= D_l.
+ *   descs, count, dtype  as hankel_plan (descriptors copied).
+ *   flags   HANKEL_SAME_X and HANKEL_STORE_SPECTRA; other bits are EINVAL.
+ * The plan computes through hankel_txv_block (forward), hankel_txv_host and
+ * hankel_txv_backward (adjoint, the k-dimensional analogue of the BHHB
+ * gradients); hankel_txv refuses it.  Synchronous.
+ * Errors: EINVAL for m or levels out of range, a non-positive size,
+ * negative offsets, unknown flags; EUNSUPPORTED for an L_l beyond the
+ * supported maximum; ENOMEM; ECUDA.
+ */
+hankel_status hankel_plan_multilevel(hankel_plan_t* out, const hankel_mdesc* descs, int64_t count,
+                                     hankel_dtype dtype, uint32_t flags);
+
+/*
  * hankel_txv -- y = H x_2 ... x_m and/or alpha = H x_1 ... x_m for every
  * descriptor (Section 3, the fast procedures for y and alpha).
  *   h, x   device buffers of generating vectors and mode vectors.
@@ -174,7 +221,8 @@ hankel_status hankel_txv_host(hankel_plan_t plan, const void* h, const void* x, 
  *   Y = vec^{-1}( H x_2 ... x_m ) = fft2(ifft2(H~) .* fft2(X~_2) ... )[0:n_1, 0:N_1],
  *   alpha = <ifft2(H~), fft2(X~_1) .* ... .* fft2(X~_m)>.
  * Buffers as hankel_txv, with column-major matrices (Section 3's vec).
- * The plan must have been made with HANKEL_BLOCK.
+ * The plan must have been made with HANKEL_BLOCK or by
+ * hankel_plan_multilevel (then the level-k products above).
  */
 hankel_status hankel_txv_block(hankel_plan_t plan, const void* H, const void* X, void* Y, void* alpha,
                                hankel_stream_t stream);

@@ -1,32 +1,37 @@
 // general.cu -- the general path: complex or real data, a different vector
-// in every mode, alpha with its own x_1, shared operands, and BHHB tensors.
+// in every mode, alpha with its own x_1, shared operands, and block tensors
+// of any level (Section 2.2: level 1 Hankel, level 2 BHHB, level k a block
+// Hankel tensor whose blocks are level-(k-1) tensors).
 //
-// Everything is expressed on P x Q spectral planes (column-major, element
-// (r, c) at r + P c).  A one-level tensor is the case Q = 1 (P = L >= d), a
-// BHHB tensor has P >= sum n - m + 1 and Q >= sum N - m + 1 (Section 3, the
-// block procedures: embed every Hankel block, then the block level).
+// Everything is expressed on k-dimensional spectral arrays of size
+// L_0 x ... x L_{k-1} (column-major: level 0 fastest, stride st_l =
+// L_0 ... L_{l-1}).  L_l >= D_l = sum_p n[l][p] - m + 1; a level whose D_l
+// is 1 keeps L_l = 1 and is never transformed.
 //
-// Forward (Section 3):
-//   1. every distinct operand gets its spectrum plane once:
-//        X^_p = fft2(X~_p),   H^ = ifft2(H~) = conj(fft2(conj H~)) / (P Q)
-//      as line transforms along dim 0 (only the operand's nonzero columns)
-//      then along dim 1 (Q > 1 only);
-//   2. per descriptor: Y~ = fft2(H^ .* X^_2 .* ... .* X^_m), transformed along
-//      dim 1 first keeping only the columns c < N_1, then along dim 0 keeping
-//      rows r < n_1 (Y = Y~[0:n_1, 0:N_1]);
-//   3. alpha = sum_{r,c} H^ .* X^_1 .* ... .* X^_m.
-// Backward (adjoint, not in the paper; G = fft2(grad_y~)):
-//   grad_H  = ifft2( sum_t G_t .* prod_p conj(X^_{t,p}(-r,-c)) )[0:d1, 0:d2]
-//   grad_X  = conj(fft2( sum_{(t,p)} H^_t .* conj(G_t(-r,-c)) .* prod_{q!=p} X^_{t,q} ))[0:n_p, 0:N_p]
+// Forward (Section 3; the k-dimensional form its closing remark states):
+//   1. every distinct operand gets its spectrum array once:
+//        X^_p = fftn(X~_p),   H^ = ifftn(G~) = conj(fftn(conj G~)) / prod L
+//      as line transforms along level 0 (over the operand's nonzero lines
+//      only), then level 1 (lines whose higher coordinates are inside the
+//      operand), and so on;
+//   2. per descriptor: Y~ = fftn(H^ .* X^_2 .* ... .* X^_m), transformed along
+//      the highest level first keeping only coordinates < n[l][0], down to
+//      level 0, whose lines store the crop Y into y;
+//   3. alpha = sum over the array of H^ .* X^_1 .* ... .* X^_m.
+// Backward (adjoint, not in the paper; G = fftn(grad_y~); (-c) is the
+// coordinate-wise negation mod L):
+//   grad_G  = ifftn( sum_t G_t .* prod_p conj(X^_{t,p}(-c)) ) cropped to D
+//   grad_X  = conj(fftn( sum_{(t,p)} H^_t .* conj(G_t(-c)) .* prod_{q!=p} X^_{t,q} )) cropped
 // where the sums run over every descriptor (and mode) that uses the operand,
 // so shared operands receive the summed gradient.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <string>
-#include <tuple>
 #include <vector>
 
 #include "fft_stage.cuh"
@@ -38,49 +43,53 @@ namespace hk {
 namespace {
 
 constexpr int MAXOPS = HANKEL_MAX_ORDER + 1;
+constexpr int MAXLV = HANKEL_MAX_LEVELS;
 
 enum { SRC_OPERAND = 0, SRC_PRODUCT = 1 };
 enum { BUF_WS = 0, BUF_OUT = 1 };
+enum { ROLE_SPECTRUM = 0, ROLE_PRODUCT = 1 };
 
 // One line transform: a block loads a line (of an input operand, or of a
-// product of spectral planes), transforms it and stores a prefix of it.
+// product of spectral arrays), transforms it and stores a prefix of it.
 struct LineTask {
     FftPlan P;
     int32_t src_mode;
     int32_t src_len, src_stride;
     int32_t src_conj;
     int64_t src;  // SRC_OPERAND: element offset in the input buffer
-    // SRC_PRODUCT: product of nops planes at coordinates along the line
-    int32_t nops, along, fixed, Pp, Qp;
-    uint32_t rev_mask;  // operand q read at (-r, -c) and conjugated
+    // SRC_PRODUCT: element i is prod_q ws[ops[q] + loff + i * lstride]
+    int32_t nops;
+    int64_t loff, lstride;
     int64_t ops[MAXOPS];
     // sink
     int32_t dst_buf, dst_len, dst_stride, dst_conj, dst_real;
     int64_t dst;
     double scale;
-    int32_t inplace;  // the sink overwrites the line the source reads
     int32_t out_sel;  // BUF_OUT sinks: 0 y, 1 grad_h, 2 grad_x
 };
 
 struct AlphaTask {
-    int32_t nops, Pp, Qp, idx;
+    int32_t nops, idx;
+    int64_t count;
     int64_t ops[MAXOPS];
 };
 
-// Elementwise spectral sum of products into one plane (backward).
+// Elementwise spectral sum of products into one array (backward).
 struct Term {
     int32_t nops;
-    uint32_t rev_mask;
+    uint32_t rev_mask;  // operand q read at (-c) and conjugated
     int64_t ops[MAXOPS];
 };
 struct AccTask {
-    int32_t Pp, Qp, t0, t1;
-    int64_t dst;
+    int32_t k, t0, t1;
+    int32_t L[MAXLV];
+    int64_t count, dst;
 };
 
 struct Launch {
     int kind;  // 0 line, 1 alpha, 2 accumulate
     int first, count, L;
+    int role;  // ROLE_SPECTRUM: spectra, always run; ROLE_PRODUCT: only when y is wanted
 };
 
 template <typename T>
@@ -100,33 +109,16 @@ struct OperandLoad {
 };
 
 template <typename T>
-__device__ __forceinline__ cx<T> plane_at(const cx<T>* ws, const int64_t* ops, int nops, uint32_t rev, int r, int c,
-                                          int P, int Q) {
-    cx<T> v = mk<T>(T(1), T(0));
-    for (int q = 0; q < nops; ++q) {
-        cx<T> w;
-        if (rev & (1u << q)) {
-            const int rr = (r == 0) ? 0 : P - r, cc = (c == 0) ? 0 : Q - c;
-            w = conjg(ws[ops[q] + rr + (int64_t)P * cc]);
-        } else {
-            w = ws[ops[q] + r + (int64_t)P * c];
-        }
-        v = (q == 0) ? w : cmul(v, w);
-    }
-    return v;
-}
-
-template <typename T>
 struct ProductLoad {
     const cx<T>* ws;
-    const int64_t* ops;  // shared-memory copy of the task's plane offsets
-    int nops, along, fixed, P, Q, len, conj;
-    uint32_t rev;
+    const int64_t* ops;  // shared-memory copy of the task's array offsets
+    int nops, len, conj;
+    int64_t loff, lstride;
     __device__ __forceinline__ cx<T> operator()(int i) const {
         if (i >= len) return mk<T>(T(0), T(0));
-        const int r = along == 0 ? i : fixed;
-        const int c = along == 0 ? fixed : i;
-        const cx<T> v = plane_at(ws, ops, nops, rev, r, c, P, Q);
+        const int64_t e = loff + (int64_t)i * lstride;
+        cx<T> v = ws[ops[0] + e];
+        for (int q = 1; q < nops; ++q) v = cmul(v, ws[ops[q] + e]);
         return conj ? conjg(v) : v;
     }
 };
@@ -150,8 +142,8 @@ struct LineSink {
 // shared-memory slots of the twiddle table (lengths up to 16384)
 constexpr int TWG_SMEM = tw_table_elems(16384);
 
-// One line per block: the line's input (an operand column/row, or a product
-// of spectral planes) is staged in shared memory, transformed by the stage
+// One line per block: the line's input (an operand line, or a product of
+// spectral arrays) is staged in shared memory, transformed by the stage
 // transform (fft_stage.cuh) and its prefix stored through the sink.  All
 // reads of the line finish before the first store, so a sink may overwrite
 // the line the source read.
@@ -176,7 +168,7 @@ __global__ void __launch_bounds__(512) line_kernel(const LineTask* __restrict__ 
         const OperandLoad<T> ld{sbase, t.src_len, t.src_stride, t.src_conj, real ? 1 : 0};
         for (int i = g.tid; i < P.L; i += g.nthr) b0[sp(i)] = ld(i);
     } else {
-        const ProductLoad<T> ld{ws, ops_s, t.nops, t.along, t.fixed, t.Pp, t.Qp, t.src_len, t.src_conj, t.rev_mask};
+        const ProductLoad<T> ld{ws, ops_s, t.nops, t.src_len, t.src_conj, t.loff, t.lstride};
         for (int i = g.tid; i < P.L; i += g.nthr) b0[sp(i)] = ld(i);
     }
     g.sync();
@@ -193,8 +185,7 @@ __global__ void __launch_bounds__(256) alpha_kernel(const AlphaTask* __restrict_
     const AlphaTask& t = tasks[first + blockIdx.x];
     const Group g{(int)threadIdx.x, (int)blockDim.x, 0};
     double sr = 0.0, si = 0.0;
-    const int64_t n = (int64_t)t.Pp * t.Qp;
-    for (int64_t e = g.tid; e < n; e += g.nthr) {
+    for (int64_t e = g.tid; e < t.count; e += g.nthr) {
         cx<double> v = mk<double>(1.0, 0.0);
         for (int q = 0; q < t.nops; ++q) {
             const cx<T> w = ws[t.ops[q] + e];
@@ -217,16 +208,83 @@ template <typename T>
 __global__ void __launch_bounds__(256) accumulate_kernel(const AccTask* __restrict__ tasks, int first,
                                                          const Term* __restrict__ terms, cx<T>* ws) {
     const AccTask& t = tasks[first + blockIdx.y];
-    const int64_t n = (int64_t)t.Pp * t.Qp;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const int r = (int)(e % t.Pp), c = (int)(e / t.Pp);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < t.count;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        // offset of the coordinate-wise negation (-c) mod L
+        int64_t re = 0, rest = e, st = 1;
+        for (int l = 0; l < t.k; ++l) {
+            const int64_t c = rest % t.L[l];
+            rest /= t.L[l];
+            re += (c == 0 ? 0 : t.L[l] - c) * st;
+            st *= t.L[l];
+        }
         cx<T> acc = mk<T>(T(0), T(0));
-        for (int k = t.t0; k < t.t1; ++k) {
-            const Term& tm = terms[k];
-            acc = acc + plane_at(ws, tm.ops, tm.nops, tm.rev_mask, r, c, t.Pp, t.Qp);
+        for (int j = t.t0; j < t.t1; ++j) {
+            const Term& tm = terms[j];
+            cx<T> v = mk<T>(T(1), T(0));
+            for (int q = 0; q < tm.nops; ++q) {
+                const cx<T> w = (tm.rev_mask & (1u << q)) ? conjg(ws[tm.ops[q] + re]) : ws[tm.ops[q] + e];
+                v = (q == 0) ? w : cmul(v, w);
+            }
+            acc = acc + v;
         }
         ws[t.dst + e] = acc;
     }
+}
+
+// Geometry of one spectral array: per-level lengths and strides.
+struct Geo {
+    int k = 1;
+    int L[MAXLV] = {1, 1, 1, 1};
+    int64_t st[MAXLV] = {1, 1, 1, 1};
+    int64_t total = 1;
+    void finish() {
+        total = 1;
+        for (int l = 0; l < k; ++l) {
+            st[l] = total;
+            total *= L[l];
+        }
+    }
+    int top() const {  // highest transformed level (level 0 always is)
+        int t = 0;
+        for (int l = 0; l < k; ++l)
+            if (L[l] > 1) t = l;
+        return t;
+    }
+};
+
+// Column-major strides of an array with extents ext[0..k).
+void cm_strides(int k, const int* ext, int64_t* st) {
+    int64_t s = 1;
+    for (int l = 0; l < k; ++l) {
+        st[l] = s;
+        s *= ext[l];
+    }
+}
+
+// Visit every line along level `l` of a k-dimensional array whose other
+// coordinates run over [0, ext[j]); the callback gets the coordinates.
+void for_lines(int k, int l, const int* ext, const std::function<void(const int*)>& fn) {
+    int c[MAXLV] = {0, 0, 0, 0};
+    for (int j = 0; j < k; ++j)
+        if (j != l && ext[j] <= 0) return;
+    while (true) {
+        fn(c);
+        int j = 0;
+        for (; j < k; ++j) {
+            if (j == l) continue;
+            if (++c[j] < ext[j]) break;
+            c[j] = 0;
+        }
+        if (j == k) return;
+    }
+}
+
+int64_t dot(int k, const int* c, const int64_t* st, int skip) {
+    int64_t o = 0;
+    for (int j = 0; j < k; ++j)
+        if (j != skip) o += (int64_t)c[j] * st[j];
+    return o;
 }
 
 }  // namespace
@@ -236,47 +294,43 @@ __global__ void __launch_bounds__(256) accumulate_kernel(const AccTask* __restri
 struct GeneralPlan {
     hankel_dtype dtype;
     uint32_t flags;
-    bool dbl, cplx, block;
-    std::vector<hankel_desc> descs;
+    bool dbl, cplx;
+    std::vector<hankel_mdesc> descs;
     struct Op {
         bool is_h;
         int64_t off;
-        int rows, cols, P, Q;
+        int rows[MAXLV];  // extents of the operand along each level
+        Geo geo;
         int64_t plane;
     };
     std::vector<Op> ops;
     struct D {
-        int m, P, Q, n1, N1, d1, d2;
+        int m;
+        Geo geo;
+        int n1[MAXLV];  // output extents
         int hop, xop[HANKEL_MAX_ORDER];  // operand index of h and x_1..x_m
         int64_t temp, gplane;
     };
     std::vector<D> ds;
     std::map<int, int> tw_off;
+    int64_t tw_elems = 0, ws_elems = 0;
     void* d_tw = nullptr;
-    cx<float>* ws32 = nullptr;
     void* d_ws = nullptr;
     size_t ws_bytes = 0;
-    // forward / backward programs
     std::vector<LineTask> fwd_lines, bwd_lines;
     std::vector<AlphaTask> alphas;
     std::vector<Term> terms;
     std::vector<AccTask> accs;
     std::vector<Launch> fwd_prog, bwd_prog_spec, bwd_prog_rest;
-    std::vector<Launch> alpha_prog;
     LineTask *d_fwd = nullptr, *d_bwd = nullptr;
     AlphaTask* d_alpha = nullptr;
     Term* d_terms = nullptr;
     AccTask* d_accs = nullptr;
-    bool want_grad_h = true, want_grad_x = true;
-    // backward gradient targets
-    std::vector<int64_t> h_targets, x_targets;  // operand indices
 };
 
 namespace {
 
 size_t csize(const GeneralPlan* g) { return (g->dbl ? 8 : 4) * 2; }
-
-int64_t fft_len(int64_t d) { return hankel_fft_length(d); }
 
 FftPlan plan_for(GeneralPlan* g, int L) {
     FftPlan P;
@@ -295,120 +349,125 @@ LineTask blank_task() {
     return t;
 }
 
-// Spectrum plane of operand o: dim-0 lines over its nonzero columns, then
-// dim-1 lines (Q > 1).  h operands become ifft2 (conj in, conj + 1/(PQ) out).
-void emit_operand_spectrum(GeneralPlan* g, int o, std::vector<LineTask>& lines, std::vector<Launch>& prog) {
-    const auto& op = g->ops[o];
-    const bool last_is_dim0 = (op.Q == 1);
-    const double sc = op.is_h ? 1.0 / ((double)op.P * op.Q) : 1.0;
-    int first = (int)lines.size();
-    for (int j = 0; j < op.cols; ++j) {
-        LineTask t = blank_task();
-        t.P = plan_for(g, op.P);
-        t.src_mode = SRC_OPERAND;
-        t.src = op.off + (int64_t)j * op.rows;
-        t.src_len = op.rows;
-        t.src_conj = op.is_h;
-        t.dst_buf = BUF_WS;
-        t.dst = op.plane + (int64_t)j * op.P;
-        t.dst_len = op.P;
-        t.dst_real = g->cplx ? 0 : 2;  // input real flag in bit 1
-        if (last_is_dim0) {
-            t.dst_conj = op.is_h;
-            t.scale = sc;
-        }
-        lines.push_back(t);
-    }
-    prog.push_back({0, first, (int)lines.size() - first, op.P});
-    if (op.Q > 1) {
-        first = (int)lines.size();
-        for (int r = 0; r < op.P; ++r) {
+// Per-level launches of a multi-phase emission: phases[l] holds the launches
+// of phase l (one per transform length).
+using Phases = std::vector<std::vector<Launch>>;
+
+void add_launch(Phases& ph, int phase, int first, int count, int L, int role) {
+    if (count == 0) return;
+    if ((int)ph.size() <= phase) ph.resize(phase + 1);
+    ph[phase].push_back({0, first, count, L, role});
+}
+
+// Spectrum array of an operand whose data (extents rows[], column-major) is
+// at `src` in the input buffer: level-0 lines read the input (zero-padded),
+// every higher transformed level works in place on the array.  For the
+// generating tensor (is_h) the result is ifftn = conj(fftn(conj .)) / total.
+void emit_spectrum(GeneralPlan* g, bool is_h, int64_t src, const int* rows, const Geo& geo, int64_t plane,
+                   std::vector<LineTask>& lines, Phases& ph) {
+    const int top = geo.top();
+    const double sc = is_h ? 1.0 / (double)geo.total : 1.0;
+    int64_t rs[MAXLV];
+    cm_strides(geo.k, rows, rs);
+    for (int l = 0; l < geo.k; ++l) {
+        if (geo.L[l] == 1) continue;
+        int ext[MAXLV];
+        for (int j = 0; j < geo.k; ++j) ext[j] = j < l ? geo.L[j] : rows[j];
+        const int first = (int)lines.size();
+        for_lines(geo.k, l, ext, [&](const int* c) {
             LineTask t = blank_task();
-            t.P = plan_for(g, op.Q);
-            t.src_mode = SRC_PRODUCT;
-            t.nops = 1;
-            t.ops[0] = op.plane;
-            t.along = 1;
-            t.fixed = r;
-            t.Pp = op.P;
-            t.Qp = op.Q;
-            t.src_len = op.cols;
+            t.P = plan_for(g, geo.L[l]);
+            if (l == 0) {
+                t.src_mode = SRC_OPERAND;
+                t.src = src + dot(geo.k, c, rs, 0);
+                t.src_conj = is_h;
+                t.dst_real = g->cplx ? 0 : 2;  // input real flag in bit 1
+            } else {
+                t.src_mode = SRC_PRODUCT;
+                t.nops = 1;
+                t.ops[0] = plane;
+                t.loff = dot(geo.k, c, geo.st, l);
+                t.lstride = geo.st[l];
+            }
+            t.src_len = rows[l];
             t.dst_buf = BUF_WS;
-            t.dst = op.plane + r;
-            t.dst_stride = op.P;
-            t.dst_len = op.Q;
-            t.dst_conj = op.is_h;
-            t.scale = sc;
-            t.inplace = 1;
+            t.dst = plane + dot(geo.k, c, geo.st, l);
+            t.dst_stride = (int)geo.st[l];
+            t.dst_len = geo.L[l];
+            if (l == top) {
+                t.dst_conj = is_h;
+                t.scale = sc;
+            }
             lines.push_back(t);
-        }
-        prog.push_back({0, first, (int)lines.size() - first, op.Q});
+        });
+        add_launch(ph, l, first, (int)lines.size() - first, geo.L[l], ROLE_SPECTRUM);
     }
 }
 
-// Two-pass transform of a product of planes, cropped to rows x cols and stored
-// to a destination matrix (column-major, leading dimension ld):
-// dim 1 first over all P rows into `temp` (keeping cols columns), then dim 0.
-void emit_product_transform(GeneralPlan* g, int P, int Q, const std::vector<int64_t>& planes, uint32_t rev,
-                            bool conj_in, int rows, int cols, int64_t temp, int dst_buf, int64_t dst, int64_t ld,
-                            bool conj_out, double scale, bool real_out, std::vector<LineTask>& lines,
-                            std::vector<Launch>& prog) {
-    if (Q > 1) {
-        int first = (int)lines.size();
-        for (int r = 0; r < P; ++r) {
+// Inverse-direction transform of a spectral array (the product of `planes`,
+// or an array already in `temp`), highest transformed level first, cropped
+// to extents out[] and finally stored along level 0 to the destination
+// (column-major with extents out[]).  Intermediate levels write into `temp`
+// (a full-size array; it may be the source array itself).
+void emit_crop_transform(GeneralPlan* g, const Geo& geo, const std::vector<int64_t>& planes, bool conj_in,
+                         const int* out, int64_t temp, int dst_buf, int64_t dst, bool conj_out, double scale,
+                         bool real_out, int out_sel, std::vector<LineTask>& lines, Phases& ph, int role) {
+    int64_t os[MAXLV];
+    cm_strides(geo.k, out, os);
+    std::vector<int> act;
+    for (int l = geo.k - 1; l >= 0; --l)
+        if (geo.L[l] > 1 || l == 0) act.push_back(l);
+    for (size_t s = 0; s < act.size(); ++s) {
+        const int l = act[s];
+        const bool first_stage = (s == 0);
+        int ext[MAXLV];
+        for (int j = 0; j < geo.k; ++j) ext[j] = j < l ? geo.L[j] : out[j];
+        const int first = (int)lines.size();
+        for_lines(geo.k, l, ext, [&](const int* c) {
             LineTask t = blank_task();
-            t.P = plan_for(g, Q);
+            t.P = plan_for(g, geo.L[l]);
             t.src_mode = SRC_PRODUCT;
-            t.nops = (int)planes.size();
-            for (int q = 0; q < t.nops; ++q) t.ops[q] = planes[q];
-            t.rev_mask = rev;
-            t.src_conj = conj_in;
-            t.along = 1;
-            t.fixed = r;
-            t.Pp = P;
-            t.Qp = Q;
-            t.src_len = Q;
-            t.dst_buf = BUF_WS;
-            t.dst = temp + r;
-            t.dst_stride = P;
-            t.dst_len = cols;
+            if (first_stage) {
+                t.nops = (int)planes.size();
+                for (int q = 0; q < t.nops; ++q) t.ops[q] = planes[q];
+                t.src_conj = conj_in;
+            } else {
+                t.nops = 1;
+                t.ops[0] = temp;
+            }
+            t.loff = dot(geo.k, c, geo.st, l);
+            t.lstride = geo.st[l];
+            t.src_len = geo.L[l];
+            if (l == 0) {
+                t.dst_buf = dst_buf;
+                t.dst = dst + dot(geo.k, c, os, 0);
+                t.dst_len = out[0];
+                t.dst_conj = conj_out;
+                t.scale = scale;
+                t.dst_real = real_out ? 1 : 0;
+                t.out_sel = out_sel;
+            } else {
+                t.dst_buf = BUF_WS;
+                t.dst = temp + t.loff;
+                t.dst_stride = (int)geo.st[l];
+                t.dst_len = out[l];
+            }
             lines.push_back(t);
-        }
-        prog.push_back({0, first, (int)lines.size() - first, Q});
+        });
+        add_launch(ph, (int)s, first, (int)lines.size() - first, geo.L[l], role);
     }
-    int first = (int)lines.size();
-    for (int c = 0; c < cols; ++c) {
-        LineTask t = blank_task();
-        t.P = plan_for(g, P);
-        t.src_mode = SRC_PRODUCT;
-        if (Q > 1) {
-            t.nops = 1;
-            t.ops[0] = temp;
-            t.Qp = cols;
-        } else {
-            t.nops = (int)planes.size();
-            for (int q = 0; q < t.nops; ++q) t.ops[q] = planes[q];
-            t.rev_mask = rev;
-            t.src_conj = conj_in;
-            t.Qp = Q;
-        }
-        t.along = 0;
-        t.fixed = c;
-        t.Pp = P;
-        t.src_len = P;
-        t.dst_buf = dst_buf;
-        t.dst = dst + (int64_t)c * ld;
-        t.dst_len = rows;
-        t.dst_conj = conj_out;
-        t.scale = scale;
-        t.dst_real = real_out ? 1 : 0;
-        lines.push_back(t);
-    }
-    prog.push_back({0, first, (int)lines.size() - first, P});
 }
 
-// Group consecutive launches of the same kind and length (independent tasks
-// of one phase) to cut launch counts.
+// Flatten phases into one program; `cuts` receives the phase boundaries.
+void flatten(const Phases& ph, std::vector<Launch>& prog, std::vector<int>& cuts) {
+    for (const auto& p : ph) {
+        prog.insert(prog.end(), p.begin(), p.end());
+        cuts.push_back((int)prog.size());
+    }
+}
+
+// Group consecutive launches of the same kind, length and role (independent
+// tasks of one phase) to cut launch counts.
 std::vector<Launch> merge(const std::vector<Launch>& in, const std::vector<int>& barriers) {
     std::vector<Launch> out;
     size_t bi = 0;
@@ -419,7 +478,7 @@ std::vector<Launch> merge(const std::vector<Launch>& in, const std::vector<int>&
             ++bi;
         }
         if (!out.empty() && !cut && out.back().kind == in[i].kind && out.back().L == in[i].L &&
-            out.back().first + out.back().count == in[i].first)
+            out.back().role == in[i].role && out.back().first + out.back().count == in[i].first)
             out.back().count += in[i].count;
         else
             out.push_back(in[i]);
@@ -469,32 +528,231 @@ int nthr_for(int L) {
 }
 
 template <typename T>
-cudaError_t run_lines(GeneralPlan* g, const std::vector<Launch>& prog, const LineTask* d_tasks, const void* in,
-                      void* out, cudaStream_t st) {
-    for (const Launch& l : prog) {
-        const size_t smem = line_smem(g, l.L);
-        // raise the limit only when needed (no attribute calls in steady state,
-        // so the launches can be captured into CUDA graphs); per device
-        static size_t granted[64] = {0};
-        int dev = 0;
-        cudaError_t e = cudaGetDevice(&dev);
+cudaError_t run_lines(GeneralPlan* g, const Launch& l, const LineTask* d_tasks, const void* in, void* out,
+                      cudaStream_t st) {
+    const size_t smem = line_smem(g, l.L);
+    // raise the limit only when needed (no attribute calls in steady state,
+    // so the launches can be captured into CUDA graphs); per device
+    static size_t granted[64] = {0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (smem > granted[dev & 63]) {
+        e = cudaFuncSetAttribute(line_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        if (smem > granted[dev & 63]) {
-            e = cudaFuncSetAttribute(line_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            granted[dev & 63] = smem;
-        }
-        line_kernel<T><<<l.count, nthr_for(l.L), smem, st>>>(d_tasks, l.first, in, out, (cx<T>*)g->d_ws,
-                                                           (const cx<T>*)g->d_tw, l.L);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+        granted[dev & 63] = smem;
     }
-    return cudaSuccess;
+    line_kernel<T><<<l.count, nthr_for(l.L), smem, st>>>(d_tasks, l.first, in, out, (cx<T>*)g->d_ws,
+                                                       (const cx<T>*)g->d_tw, l.L);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
-hankel_status general_create(GeneralPlan** out, const std::vector<hankel_desc>& descs, hankel_dtype dtype,
+namespace {
+
+// Host half of plan creation: operands, array offsets, twiddle offsets and
+// the launch programs.  Touches no device (the task tables can be built and
+// inspected without a GPU).
+hankel_status build_programs(GeneralPlan* g, const std::vector<hankel_mdesc>& descs, int64_t* h_elems,
+                             int64_t* x_elems, int64_t* y_elems, int64_t* sum_L, int64_t* max_L, std::string& err) {
+    const bool same_x = (g->flags & HANKEL_SAME_X) != 0;
+    const size_t cs = csize(g);
+    int maxL = 2;
+    while (maxL < 16384 && RED_BYTES + ((size_t)TWG_SMEM + 2 * smem_elems_host(maxL + 1)) * cs <= 227 * 1024) ++maxL;
+    std::map<std::vector<int64_t>, int> opidx;
+    int64_t cursor = 0;
+    auto add_op = [&](bool is_h, int64_t off, const int* rows, const Geo& geo) {
+        std::vector<int64_t> key{(int64_t)is_h, off, geo.k};
+        for (int l = 0; l < geo.k; ++l) {
+            key.push_back(rows[l]);
+            key.push_back(geo.L[l]);
+        }
+        auto it = opidx.find(key);
+        if (it != opidx.end()) return it->second;
+        GeneralPlan::Op op;
+        op.is_h = is_h;
+        op.off = off;
+        for (int l = 0; l < MAXLV; ++l) op.rows[l] = l < geo.k ? rows[l] : 1;
+        op.geo = geo;
+        op.plane = cursor;
+        cursor += geo.total;
+        g->ops.push_back(op);
+        opidx[key] = (int)g->ops.size() - 1;
+        return (int)g->ops.size() - 1;
+    };
+    *h_elems = *x_elems = *y_elems = 0;
+    *sum_L = *max_L = 0;
+    for (size_t i = 0; i < descs.size(); ++i) {
+        const hankel_mdesc& d = descs[i];
+        GeneralPlan::D D{};
+        D.m = d.m;
+        D.geo.k = d.levels;
+        int gs[MAXLV];
+        for (int l = 0; l < d.levels; ++l) {
+            int64_t s = 0;
+            for (int p = 0; p < d.m; ++p) s += d.n[l][p];
+            gs[l] = (int)(s - d.m + 1);
+            // level 0 is always transformed (length >= 2); a level with D_l = 1 is not
+            const int64_t L = (l > 0 && gs[l] == 1) ? 1 : hankel_fft_length(gs[l]);
+            FftPlan probe;
+            if (L < 0 || L > maxL || (L > 1 && !fft_factor((int)L, &probe))) {
+                err = "descriptor " + std::to_string(i) + ": FFT length beyond the supported maximum of this build";
+                return HANKEL_EUNSUPPORTED;
+            }
+            D.geo.L[l] = (int)L;
+            D.n1[l] = d.n[l][0];
+            if (L > 1) g->tw_off[(int)L] = 0;
+            *max_L = std::max<int64_t>(*max_L, L);
+        }
+        D.geo.finish();
+        if (D.geo.total > INT32_MAX) {
+            err = "descriptor " + std::to_string(i) + ": padded array of " + std::to_string(D.geo.total) +
+                  " elements exceeds this build's 2^31 limit";
+            return HANKEL_EUNSUPPORTED;
+        }
+        D.hop = add_op(true, d.h_off, gs, D.geo);
+        int64_t hsz = 1, ysz = 1;
+        for (int l = 0; l < d.levels; ++l) {
+            hsz *= gs[l];
+            ysz *= D.n1[l];
+        }
+        for (int p = 0; p < d.m; ++p) {
+            const int q = same_x ? 0 : p;
+            const int64_t xo = d.x_off[q];
+            int rows[MAXLV];
+            int64_t xsz = 1;
+            for (int l = 0; l < d.levels; ++l) {
+                rows[l] = d.n[l][q];
+                xsz *= rows[l];
+            }
+            D.xop[p] = add_op(false, xo, rows, D.geo);
+            *x_elems = std::max<int64_t>(*x_elems, xo + xsz);
+        }
+        *h_elems = std::max<int64_t>(*h_elems, d.h_off + hsz);
+        *y_elems = std::max<int64_t>(*y_elems, d.y_off + ysz);
+        *sum_L += D.geo.total;
+        g->ds.push_back(D);
+    }
+    // temp arrays (forward, more than one transformed level), G arrays and
+    // S arrays (backward)
+    for (auto& D : g->ds) {
+        D.temp = cursor;
+        if (D.geo.top() > 0) cursor += D.geo.total;
+        D.gplane = cursor;
+        cursor += D.geo.total;
+    }
+    std::vector<int64_t> splane(g->ops.size());
+    for (size_t o = 0; o < g->ops.size(); ++o) {
+        splane[o] = cursor;
+        cursor += g->ops[o].geo.total;
+    }
+    // twiddle table offsets (the tables are generated on the device later)
+    int64_t tw_total = 0;
+    for (auto& kv : g->tw_off) {
+        kv.second = (int)tw_total;
+        tw_total += tw_table_elems(kv.first);
+    }
+    g->tw_elems = tw_total;
+    g->ws_elems = cursor;
+
+    // ---- forward program: operand spectra by level, then product stages
+    {
+        Phases spec, prod;
+        for (const auto& op : g->ops) emit_spectrum(g, op.is_h, op.off, op.rows, op.geo, op.plane, g->fwd_lines, spec);
+        for (size_t i = 0; i < g->ds.size(); ++i) {
+            const auto& D = g->ds[i];
+            std::vector<int64_t> planes{g->ops[D.hop].plane};
+            for (int p = 1; p < D.m; ++p) planes.push_back(g->ops[D.xop[p]].plane);
+            emit_crop_transform(g, D.geo, planes, false, D.n1, D.temp, BUF_OUT, descs[i].y_off, false, 1.0, !g->cplx, 0,
+                                g->fwd_lines, prod, ROLE_PRODUCT);
+        }
+        std::vector<Launch> prog;
+        std::vector<int> cuts;
+        flatten(spec, prog, cuts);
+        flatten(prod, prog, cuts);
+        compact(g->fwd_lines, {&prog});
+        g->fwd_prog = merge(prog, cuts);
+    }
+    for (size_t i = 0; i < g->ds.size(); ++i) {
+        const auto& D = g->ds[i];
+        AlphaTask a;
+        std::memset(&a, 0, sizeof(a));
+        a.nops = D.m + 1;
+        a.ops[0] = g->ops[D.hop].plane;
+        for (int p = 0; p < D.m; ++p) a.ops[1 + p] = g->ops[D.xop[p]].plane;
+        a.count = D.geo.total;
+        a.idx = (int)i;
+        g->alphas.push_back(a);
+    }
+
+    // ---- backward program: spectra, G arrays, spectral sums, gradients
+    {
+        Phases bspec, gspec, tails;
+        for (const auto& op : g->ops)
+            emit_spectrum(g, op.is_h, op.off, op.rows, op.geo, op.plane, g->bwd_lines, bspec);
+        for (size_t i = 0; i < g->ds.size(); ++i) {
+            const auto& D = g->ds[i];
+            emit_spectrum(g, false, descs[i].y_off, D.n1, D.geo, D.gplane, g->bwd_lines, gspec);
+        }
+        std::vector<std::vector<Term>> hterms(g->ops.size()), xterms(g->ops.size());
+        for (const auto& D : g->ds) {
+            Term th;
+            std::memset(&th, 0, sizeof(th));
+            th.ops[th.nops++] = D.gplane;
+            for (int p = 1; p < D.m; ++p) {
+                th.rev_mask |= 1u << th.nops;
+                th.ops[th.nops++] = g->ops[D.xop[p]].plane;
+            }
+            hterms[D.hop].push_back(th);
+            for (int p = 1; p < D.m; ++p) {
+                Term tx;
+                std::memset(&tx, 0, sizeof(tx));
+                tx.ops[tx.nops++] = g->ops[D.hop].plane;
+                tx.rev_mask |= 1u << tx.nops;
+                tx.ops[tx.nops++] = D.gplane;
+                for (int q = 1; q < D.m; ++q)
+                    if (q != p) tx.ops[tx.nops++] = g->ops[D.xop[q]].plane;
+                xterms[D.xop[p]].push_back(tx);
+            }
+        }
+        for (size_t o = 0; o < g->ops.size(); ++o) {
+            const auto& op = g->ops[o];
+            const auto& tl = op.is_h ? hterms[o] : xterms[o];
+            if (tl.empty()) continue;
+            AccTask a;
+            std::memset(&a, 0, sizeof(a));
+            a.k = op.geo.k;
+            for (int l = 0; l < MAXLV; ++l) a.L[l] = l < op.geo.k ? op.geo.L[l] : 1;
+            a.count = op.geo.total;
+            a.t0 = (int)g->terms.size();
+            g->terms.insert(g->terms.end(), tl.begin(), tl.end());
+            a.t1 = (int)g->terms.size();
+            a.dst = splane[o];
+            g->accs.push_back(a);
+            // grad_G = ifftn(S) = conj(fftn(conj S)) / total; grad_X = conj(fftn(S)); both cropped
+            const bool h = op.is_h;
+            emit_crop_transform(g, op.geo, {splane[o]}, h, op.rows, splane[o], BUF_OUT, op.off, true,
+                                h ? 1.0 / (double)op.geo.total : 1.0, !g->cplx, h ? 1 : 2, g->bwd_lines, tails,
+                                ROLE_PRODUCT);
+        }
+        std::vector<Launch> spec_list, rest;
+        std::vector<int> spec_cuts, rest_cuts;
+        flatten(bspec, spec_list, spec_cuts);
+        flatten(gspec, rest, rest_cuts);
+        if (!g->accs.empty()) rest.push_back({2, 0, (int)g->accs.size(), 0, ROLE_PRODUCT});
+        rest_cuts.push_back((int)rest.size());
+        flatten(tails, rest, rest_cuts);
+        compact(g->bwd_lines, {&spec_list, &rest});
+        g->bwd_prog_spec = merge(spec_list, spec_cuts);
+        g->bwd_prog_rest = merge(rest, rest_cuts);
+    }
+    return HANKEL_OK;
+}
+
+}  // namespace
+
+hankel_status general_create(GeneralPlan** out, const std::vector<hankel_mdesc>& descs, hankel_dtype dtype,
                              uint32_t flags, int64_t* h_elems, int64_t* x_elems, int64_t* y_elems, int64_t* sum_L,
                              int64_t* max_L, std::string& err) {
     *out = nullptr;
@@ -503,315 +761,25 @@ hankel_status general_create(GeneralPlan** out, const std::vector<hankel_desc>& 
     g->flags = flags;
     g->dbl = (dtype == HANKEL_R64 || dtype == HANKEL_C128);
     g->cplx = (dtype == HANKEL_C64 || dtype == HANKEL_C128);
-    g->block = (flags & HANKEL_BLOCK) != 0;
     g->descs = descs;
-    const bool same_x = (flags & HANKEL_SAME_X) != 0;
+    hankel_status s = build_programs(g, descs, h_elems, x_elems, y_elems, sum_L, max_L, err);
+    if (s != HANKEL_OK) {
+        delete g;
+        return s;
+    }
     const size_t cs = csize(g);
-    const int maxL = (int)std::min<int64_t>(16384, [&] {
-        int L = 2;
-        while (L < 16384 && RED_BYTES + ((size_t)TWG_SMEM + 2 * smem_elems_host(L + 1)) * cs <= 227 * 1024) ++L;
-        return (int64_t)L;
-    }());
-    std::map<std::tuple<int, int64_t, int, int, int, int>, int> opidx;
-    int64_t plane_cursor = 0;
-    auto add_op = [&](bool is_h, int64_t off, int rows, int cols, int P, int Q) {
-        auto key = std::make_tuple((int)is_h, off, rows, cols, P, Q);
-        auto it = opidx.find(key);
-        if (it != opidx.end()) return it->second;
-        GeneralPlan::Op op{is_h, off, rows, cols, P, Q, plane_cursor};
-        plane_cursor += (int64_t)P * Q;
-        g->ops.push_back(op);
-        opidx[key] = (int)g->ops.size() - 1;
-        return (int)g->ops.size() - 1;
-    };
-    *h_elems = *x_elems = *y_elems = 0;
-    *sum_L = *max_L = 0;
-    for (size_t i = 0; i < descs.size(); ++i) {
-        const hankel_desc& d = descs[i];
-        GeneralPlan::D D;
-        std::memset(&D, 0, sizeof(D));
-        D.m = d.m;
-        int64_t sn = 0, sN = 0;
-        for (int p = 0; p < d.m; ++p) {
-            sn += d.n[p];
-            sN += g->block ? d.N[p] : 1;
-        }
-        D.d1 = (int)(sn - d.m + 1);
-        D.d2 = (int)(sN - d.m + 1);
-        const int64_t P = fft_len(D.d1), Q = g->block ? fft_len(D.d2) : 1;
-        if (P < 0 || Q < 0 || P > maxL || Q > maxL) {
-            err = "descriptor " + std::to_string(i) + ": FFT length beyond the supported maximum of this build";
-            delete g;
-            return HANKEL_EUNSUPPORTED;
-        }
-        D.P = (int)P;
-        D.Q = (int)Q;
-        D.n1 = d.n[0];
-        D.N1 = g->block ? d.N[0] : 1;
-        D.hop = add_op(true, d.h_off, D.d1, D.d2, D.P, D.Q);
-        for (int p = 0; p < d.m; ++p) {
-            const int64_t xo = same_x ? d.x_off[0] : d.x_off[p];
-            const int Np = g->block ? d.N[p] : 1;
-            const int np_ = same_x ? d.n[0] : d.n[p];
-            D.xop[p] = add_op(false, xo, np_, same_x ? (g->block ? d.N[0] : 1) : Np, D.P, D.Q);
-            *x_elems = std::max<int64_t>(*x_elems, xo + (int64_t)np_ * Np);
-        }
-        *h_elems = std::max<int64_t>(*h_elems, d.h_off + (int64_t)D.d1 * D.d2);
-        *y_elems = std::max<int64_t>(*y_elems, d.y_off + (int64_t)D.n1 * D.N1);
-        *sum_L += P * Q;
-        *max_L = std::max<int64_t>(*max_L, std::max(P, Q));
-        g->tw_off[(int)P] = 0;
-        g->tw_off[(int)Q] = 0;
-        g->ds.push_back(D);
-    }
-    // temp planes (forward, BHHB only), G planes and S planes (backward)
-    for (auto& D : g->ds) {
-        D.temp = plane_cursor;
-        if (D.Q > 1) plane_cursor += (int64_t)D.P * D.N1;
-        D.gplane = plane_cursor;
-        plane_cursor += (int64_t)D.P * D.Q;
-    }
-    std::vector<int64_t> splane(g->ops.size());
-    for (size_t o = 0; o < g->ops.size(); ++o) {
-        splane[o] = plane_cursor;
-        plane_cursor += (int64_t)g->ops[o].P * g->ops[o].Q;
-    }
-    // twiddles
-    int64_t tw_total = 0;
-    for (auto& kv : g->tw_off) {
-        kv.second = (int)tw_total;
-        tw_total += tw_table_elems(kv.first);
-    }
-    cudaError_t e = cudaMalloc(&g->d_tw, std::max<int64_t>(tw_total, 1) * cs);
+    cudaError_t e = cudaMalloc(&g->d_tw, std::max<int64_t>(g->tw_elems, 1) * cs);
     if (e != cudaSuccess) { delete g; return cuerr(e, "cudaMalloc(twiddles)", err); }
     for (auto& kv : g->tw_off) {
-        if (kv.first < 2) continue;  // Q = 1: no transform along that axis
         FftPlan TP;
         std::memset(&TP, 0, sizeof(TP));
         TP.L = kv.first;
         e = launch_stage_twiddles(g->dbl, (char*)g->d_tw + (size_t)kv.second * cs, TP, 0);
         if (e != cudaSuccess) { general_destroy(g); return cuerr(e, "twiddle kernel", err); }
     }
-    g->ws_bytes = (size_t)std::max<int64_t>(plane_cursor, 1) * cs;
+    g->ws_bytes = (size_t)std::max<int64_t>(g->ws_elems, 1) * cs;
     e = cudaMalloc(&g->d_ws, g->ws_bytes);
     if (e != cudaSuccess) { general_destroy(g); return cuerr(e, "cudaMalloc(workspace)", err); }
-
-    // ---- forward program
-    std::vector<Launch> prog;
-    std::vector<int> cuts;
-    for (size_t o = 0; o < g->ops.size(); ++o) emit_operand_spectrum(g, (int)o, g->fwd_lines, prog);
-    // keep spectra dim-0 / dim-1 phases ordered: cut between phases by
-    // reordering: all dim-0 launches first, then all dim-1 launches
-    {
-        std::vector<Launch> d0, d1;
-        for (auto& l : prog) {
-            const LineTask& t = g->fwd_lines[l.first];
-            ((t.src_mode == SRC_OPERAND) ? d0 : d1).push_back(l);
-        }
-        prog = d0;
-        cuts.push_back((int)prog.size());
-        prog.insert(prog.end(), d1.begin(), d1.end());
-        cuts.push_back((int)prog.size());
-    }
-    const size_t spec_end = prog.size();
-    std::vector<Launch> pd1, pd0;
-    for (size_t i = 0; i < g->ds.size(); ++i) {
-        const auto& D = g->ds[i];
-        std::vector<int64_t> planes{g->ops[D.hop].plane};
-        for (int p = 1; p < D.m; ++p) planes.push_back(g->ops[D.xop[p]].plane);
-        std::vector<Launch> tmp;
-        emit_product_transform(g, D.P, D.Q, planes, 0u, false, D.n1, D.N1, D.temp, BUF_OUT, descs[i].y_off, D.n1,
-                               false, 1.0, !g->cplx, g->fwd_lines, tmp);
-        if (tmp.size() == 2) {
-            pd1.push_back(tmp[0]);
-            pd0.push_back(tmp[1]);
-        } else {
-            pd0.push_back(tmp[0]);
-        }
-    }
-    prog.insert(prog.end(), pd1.begin(), pd1.end());
-    cuts.push_back((int)prog.size());
-    prog.insert(prog.end(), pd0.begin(), pd0.end());
-    compact(g->fwd_lines, {&prog});
-    g->fwd_prog = merge(prog, cuts);
-    (void)spec_end;
-    for (size_t i = 0; i < g->ds.size(); ++i) {
-        const auto& D = g->ds[i];
-        AlphaTask a;
-        std::memset(&a, 0, sizeof(a));
-        a.nops = D.m + 1;
-        a.ops[0] = g->ops[D.hop].plane;
-        for (int p = 0; p < D.m; ++p) a.ops[1 + p] = g->ops[D.xop[p]].plane;
-        a.Pp = D.P;
-        a.Qp = D.Q;
-        a.idx = (int)i;
-        g->alphas.push_back(a);
-    }
-
-    // ---- backward program: G planes, spectral sums, transforms to gradients
-    std::vector<Launch> bspec, bg0, bg1, spec_list;
-    std::vector<int> spec_cuts;
-    for (size_t o = 0; o < g->ops.size(); ++o) emit_operand_spectrum(g, (int)o, g->bwd_lines, bspec);
-    {
-        std::vector<Launch> d0, d1;
-        for (auto& l : bspec) ((g->bwd_lines[l.first].src_mode == SRC_OPERAND) ? d0 : d1).push_back(l);
-        std::vector<int> c2{(int)d0.size()};
-        d0.insert(d0.end(), d1.begin(), d1.end());
-        c2.push_back((int)d0.size());
-        spec_list = d0;
-        spec_cuts = c2;
-    }
-    // G_t = fft2(grad_y~): dim-0 over the N1 nonzero columns, then dim 1
-    for (size_t i = 0; i < g->ds.size(); ++i) {
-        const auto& D = g->ds[i];
-        int first = (int)g->bwd_lines.size();
-        for (int c = 0; c < D.N1; ++c) {
-            LineTask t = blank_task();
-            t.P = plan_for(g, D.P);
-            t.src_mode = SRC_OPERAND;
-            t.src = descs[i].y_off + (int64_t)c * D.n1;
-            t.src_len = D.n1;
-            t.dst_buf = BUF_WS;
-            t.dst = D.gplane + (int64_t)c * D.P;
-            t.dst_len = D.P;
-            t.dst_real = g->cplx ? 0 : 2;
-            g->bwd_lines.push_back(t);
-        }
-        bg0.push_back({0, first, (int)g->bwd_lines.size() - first, D.P});
-        if (D.Q > 1) {
-            first = (int)g->bwd_lines.size();
-            for (int r = 0; r < D.P; ++r) {
-                LineTask t = blank_task();
-                t.P = plan_for(g, D.Q);
-                t.src_mode = SRC_PRODUCT;
-                t.nops = 1;
-                t.ops[0] = D.gplane;
-                t.along = 1;
-                t.fixed = r;
-                t.Pp = D.P;
-                t.Qp = D.Q;
-                t.src_len = D.N1;
-                t.dst_buf = BUF_WS;
-                t.dst = D.gplane + r;
-                t.dst_stride = D.P;
-                t.dst_len = D.Q;
-                t.inplace = 1;
-                g->bwd_lines.push_back(t);
-            }
-            bg1.push_back({0, first, (int)g->bwd_lines.size() - first, D.Q});
-        }
-    }
-    // spectral sums per gradient target
-    std::vector<std::vector<Term>> hterms(g->ops.size()), xterms(g->ops.size());
-    for (size_t i = 0; i < g->ds.size(); ++i) {
-        const auto& D = g->ds[i];
-        Term th;
-        std::memset(&th, 0, sizeof(th));
-        th.ops[th.nops++] = D.gplane;
-        for (int p = 1; p < D.m; ++p) {
-            th.rev_mask |= 1u << th.nops;
-            th.ops[th.nops++] = g->ops[D.xop[p]].plane;
-        }
-        hterms[D.hop].push_back(th);
-        for (int p = 1; p < D.m; ++p) {
-            Term tx;
-            std::memset(&tx, 0, sizeof(tx));
-            tx.ops[tx.nops++] = g->ops[D.hop].plane;
-            tx.rev_mask |= 1u << tx.nops;
-            tx.ops[tx.nops++] = D.gplane;
-            for (int q = 1; q < D.m; ++q)
-                if (q != p) tx.ops[tx.nops++] = g->ops[D.xop[q]].plane;
-            xterms[D.xop[p]].push_back(tx);
-        }
-    }
-    std::vector<Launch> bacc;
-    std::vector<LineTask> tail_lines;
-    std::vector<Launch> bt1, bt0;
-    for (size_t o = 0; o < g->ops.size(); ++o) {
-        const auto& op = g->ops[o];
-        const auto& tl = op.is_h ? hterms[o] : xterms[o];
-        if (tl.empty()) continue;
-        AccTask a;
-        a.Pp = op.P;
-        a.Qp = op.Q;
-        a.t0 = (int)g->terms.size();
-        g->terms.insert(g->terms.end(), tl.begin(), tl.end());
-        a.t1 = (int)g->terms.size();
-        a.dst = splane[o];
-        g->accs.push_back(a);
-        (op.is_h ? g->h_targets : g->x_targets).push_back((int64_t)o);
-        // grad_h = ifft2(S) = conj(fft2(conj S))/(PQ); grad_x = conj(fft2(S)); both cropped
-        std::vector<Launch> tmp;
-        const bool h = op.is_h;
-        const int64_t temp = splane[o];  // dim-1 pass writes back into S (its first `cols` columns)
-        if (op.Q > 1) {
-            // dim 1 in place on S (conj in for h), keep the first `cols` columns
-            int first = (int)g->bwd_lines.size();
-            for (int r = 0; r < op.P; ++r) {
-                LineTask t = blank_task();
-                t.P = plan_for(g, op.Q);
-                t.src_mode = SRC_PRODUCT;
-                t.nops = 1;
-                t.ops[0] = splane[o];
-                t.src_conj = h;
-                t.along = 1;
-                t.fixed = r;
-                t.Pp = op.P;
-                t.Qp = op.Q;
-                t.src_len = op.Q;
-                t.dst_buf = BUF_WS;
-                t.dst = splane[o] + r;
-                t.dst_stride = op.P;
-                t.dst_len = op.cols;
-                t.inplace = 1;
-                g->bwd_lines.push_back(t);
-            }
-            bt1.push_back({0, first, (int)g->bwd_lines.size() - first, op.Q});
-        }
-        int first = (int)g->bwd_lines.size();
-        for (int c = 0; c < op.cols; ++c) {
-            LineTask t = blank_task();
-            t.P = plan_for(g, op.P);
-            t.src_mode = SRC_PRODUCT;
-            t.nops = 1;
-            t.ops[0] = temp;
-            t.src_conj = (op.Q > 1) ? 0 : h;
-            t.along = 0;
-            t.fixed = c;
-            t.Pp = op.P;
-            t.Qp = op.Q;
-            t.src_len = op.P;
-            t.dst_buf = BUF_OUT;
-            t.dst = (h ? 0 : 0) + op.off + (int64_t)c * op.rows;
-            t.dst_len = op.rows;
-            t.dst_conj = 1;
-            t.scale = h ? 1.0 / ((double)op.P * op.Q) : 1.0;
-            t.dst_real = g->cplx ? 0 : 1;
-            t.out_sel = h ? 1 : 2;
-            g->bwd_lines.push_back(t);
-            (void)tmp;
-        }
-        bt0.push_back({0, first, (int)g->bwd_lines.size() - first, op.P});
-        bacc.push_back({2, (int)g->accs.size() - 1, 1, 0});
-    }
-    {
-        std::vector<Launch> rest;
-        std::vector<int> c3;
-        rest.insert(rest.end(), bg0.begin(), bg0.end());
-        c3.push_back((int)rest.size());
-        rest.insert(rest.end(), bg1.begin(), bg1.end());
-        c3.push_back((int)rest.size());
-        // accumulate launches are emitted as one launch over all targets
-        if (!g->accs.empty()) rest.push_back({2, 0, (int)g->accs.size(), 0});
-        c3.push_back((int)rest.size());
-        rest.insert(rest.end(), bt1.begin(), bt1.end());
-        c3.push_back((int)rest.size());
-        rest.insert(rest.end(), bt0.begin(), bt0.end());
-        compact(g->bwd_lines, {&spec_list, &rest});
-        g->bwd_prog_spec = merge(spec_list, spec_cuts);
-        g->bwd_prog_rest = merge(rest, c3);
-    }
-    hankel_status s;
     if ((s = upload(g->fwd_lines, &g->d_fwd, err)) != HANKEL_OK) { general_destroy(g); return s; }
     if ((s = upload(g->bwd_lines, &g->d_bwd, err)) != HANKEL_OK) { general_destroy(g); return s; }
     if ((s = upload(g->alphas, &g->d_alpha, err)) != HANKEL_OK) { general_destroy(g); return s; }
@@ -823,40 +791,55 @@ hankel_status general_create(GeneralPlan** out, const std::vector<hankel_desc>& 
     return HANKEL_OK;
 }
 
+namespace {
+
+// Run the line launches of a program.  Launches reading input operands are
+// split into runs of generating-tensor operands (read from `h`, conjugated
+// on load) and vector operands (read from `x`).
+template <typename Skip, typename Run>
+cudaError_t run_program(GeneralPlan* g, const std::vector<Launch>& prog, const std::vector<LineTask>& lines,
+                        Skip skip, Run run) {
+    for (const Launch& l : prog) {
+        if (skip(l)) continue;
+        if (l.kind != 0) {
+            cudaError_t e = run(l, 0);
+            if (e != cudaSuccess) return e;
+            continue;
+        }
+        int i = l.first;
+        while (i < l.first + l.count) {
+            int j = i + 1;
+            int what = 0;  // 0 workspace source, 1 h operand, 2 x operand, 3 + sel output sink
+            auto cls = [&](const LineTask& t) {
+                if (t.dst_buf == BUF_OUT && t.out_sel != 0) return 3 + t.out_sel;
+                if (t.src_mode == SRC_OPERAND) return t.src_conj ? 1 : 2;
+                return 0;
+            };
+            what = cls(lines[i]);
+            while (j < l.first + l.count && cls(lines[j]) == what) ++j;
+            cudaError_t e = run({0, i, j - i, l.L, l.role}, what);
+            if (e != cudaSuccess) return e;
+            i = j;
+        }
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
 hankel_status general_forward(GeneralPlan* g, const void* h, const void* x, void* y, void* alpha, cudaStream_t st,
                               std::string& err) {
     if (!g) {
         err = "plan has no general program";
         return HANKEL_EINVAL;
     }
-    // phase 1: operand spectra (h operands read `h`, x operands read `x`)
-    cudaError_t e = cudaSuccess;
-    for (const Launch& l : g->fwd_prog) {
-        const LineTask& t0 = g->fwd_lines[l.first];
-        const bool spectra = (t0.dst_buf == BUF_WS && (t0.src_mode == SRC_OPERAND || t0.inplace));
-        if (!spectra && y == nullptr) continue;  // product transforms only when y is wanted
-        // launches mix h and x operands; split by operand kind within the launch
-        int i = l.first;
-        while (i < l.first + l.count) {
-            int j = i;
-            bool ish = false;
-            if (g->fwd_lines[i].src_mode == SRC_OPERAND) {
-                // find operand kind from its conj flag (h operands are conjugated on load)
-                ish = g->fwd_lines[i].src_conj != 0;
-                while (j < l.first + l.count && g->fwd_lines[j].src_mode == SRC_OPERAND &&
-                       (g->fwd_lines[j].src_conj != 0) == ish)
-                    ++j;
-            } else {
-                j = l.first + l.count;
-            }
-            Launch sub{0, i, j - i, l.L};
-            std::vector<Launch> one{sub};
-            e = g->dbl ? run_lines<double>(g, one, g->d_fwd, ish ? h : x, y, st)
-                       : run_lines<float>(g, one, g->d_fwd, ish ? h : x, y, st);
-            if (e != cudaSuccess) return cuerr(e, "general forward launch", err);
-            i = j;
-        }
-    }
+    cudaError_t e = run_program(
+        g, g->fwd_prog, g->fwd_lines, [&](const Launch& l) { return l.role == ROLE_PRODUCT && y == nullptr; },
+        [&](const Launch& l, int what) {
+            const void* in = (what == 1) ? h : x;
+            return g->dbl ? run_lines<double>(g, l, g->d_fwd, in, y, st) : run_lines<float>(g, l, g->d_fwd, in, y, st);
+        });
+    if (e != cudaSuccess) return cuerr(e, "general forward launch", err);
     if (alpha != nullptr) {
         if (g->dbl)
             alpha_kernel<double><<<(int)g->alphas.size(), 256, 0, st>>>(g->d_alpha, 0, (const cx<double>*)g->d_ws,
@@ -876,63 +859,36 @@ hankel_status general_backward(GeneralPlan* g, const void* gy, const void* h, co
         err = "plan has no general program";
         return HANKEL_EINVAL;
     }
-    cudaError_t e;
-    auto run_sub = [&](const Launch& l, const void* in, void* out) {
-        std::vector<Launch> one{l};
-        return g->dbl ? run_lines<double>(g, one, g->d_bwd, in, out, st)
-                      : run_lines<float>(g, one, g->d_bwd, in, out, st);
+    auto lines = [&](const Launch& l, const void* in, void* out) {
+        return g->dbl ? run_lines<double>(g, l, g->d_bwd, in, out, st) : run_lines<float>(g, l, g->d_bwd, in, out, st);
     };
+    cudaError_t e = cudaSuccess;
     if (!(g->flags & HANKEL_STORE_SPECTRA)) {
-        for (const Launch& l : g->bwd_prog_spec) {
-            int i = l.first;
-            while (i < l.first + l.count) {
-                int j = i;
-                bool ish = false;
-                if (g->bwd_lines[i].src_mode == SRC_OPERAND) {
-                    ish = g->bwd_lines[i].src_conj != 0;
-                    while (j < l.first + l.count && g->bwd_lines[j].src_mode == SRC_OPERAND &&
-                           (g->bwd_lines[j].src_conj != 0) == ish)
-                        ++j;
-                } else {
-                    j = l.first + l.count;
-                }
-                e = run_sub({0, i, j - i, l.L}, ish ? h : x, nullptr);
-                if (e != cudaSuccess) return cuerr(e, "backward spectra launch", err);
-                i = j;
-            }
-        }
+        e = run_program(
+            g, g->bwd_prog_spec, g->bwd_lines, [](const Launch&) { return false; },
+            [&](const Launch& l, int what) { return lines(l, what == 1 ? h : x, nullptr); });
+        if (e != cudaSuccess) return cuerr(e, "backward spectra launch", err);
     }
-    for (const Launch& l : g->bwd_prog_rest) {
-        if (l.kind == 2) {
-            dim3 grid(64, l.count);
-            if (g->dbl)
-                accumulate_kernel<double><<<grid, 256, 0, st>>>(g->d_accs, l.first, g->d_terms, (cx<double>*)g->d_ws);
-            else
-                accumulate_kernel<float><<<grid, 256, 0, st>>>(g->d_accs, l.first, g->d_terms, (cx<float>*)g->d_ws);
-            e = cudaGetLastError();
-            if (e != cudaSuccess) return cuerr(e, "accumulate launch", err);
-            continue;
-        }
-        const LineTask& t0 = g->bwd_lines[l.first];
-        if (t0.dst_buf == BUF_OUT) {
-            // gradient stores: split the launch into grad_h and grad_x runs
-            int i = l.first;
-            while (i < l.first + l.count) {
-                const int sel = g->bwd_lines[i].out_sel;
-                int j = i + 1;
-                while (j < l.first + l.count && g->bwd_lines[j].out_sel == sel) ++j;
-                void* dst = (sel == 1) ? gh : gx;
-                if (dst != nullptr) {
-                    e = run_sub({0, i, j - i, l.L}, nullptr, dst);
-                    if (e != cudaSuccess) return cuerr(e, "backward launch", err);
-                }
-                i = j;
+    e = run_program(
+        g, g->bwd_prog_rest, g->bwd_lines, [](const Launch&) { return false; },
+        [&](const Launch& l, int what) -> cudaError_t {
+            if (l.kind == 2) {
+                dim3 grid(64, l.count);
+                if (g->dbl)
+                    accumulate_kernel<double><<<grid, 256, 0, st>>>(g->d_accs, l.first, g->d_terms,
+                                                                    (cx<double>*)g->d_ws);
+                else
+                    accumulate_kernel<float><<<grid, 256, 0, st>>>(g->d_accs, l.first, g->d_terms,
+                                                                   (cx<float>*)g->d_ws);
+                return cudaGetLastError();
             }
-        } else {
-            e = run_sub(l, gy, nullptr);
-            if (e != cudaSuccess) return cuerr(e, "backward launch", err);
-        }
-    }
+            if (what >= 3) {  // gradient stores: grad_h (sel 1) or grad_x (sel 2)
+                void* dst = (what == 4) ? gh : gx;
+                return dst ? lines(l, nullptr, dst) : cudaSuccess;
+            }
+            return lines(l, gy, nullptr);  // G arrays read grad_y; the rest read workspace
+        });
+    if (e != cudaSuccess) return cuerr(e, "backward launch", err);
     return HANKEL_OK;
 }
 

@@ -1,6 +1,7 @@
 // general.h -- the general path: complex data, distinct mode vectors, alpha
-// with its own x_1, and BHHB tensors.  Spectra of every distinct operand are
-// computed once into plan workspace, then each product is one transform.
+// with its own x_1, and block Hankel tensors of any level (BHHB is level 2).
+// Spectra of every distinct operand are computed once into plan workspace,
+// then each product is one k-dimensional transform.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -14,7 +15,7 @@ namespace hk {
 
 struct GeneralPlan;
 
-hankel_status general_create(GeneralPlan** out, const std::vector<hankel_desc>& descs, hankel_dtype dtype,
+hankel_status general_create(GeneralPlan** out, const std::vector<hankel_mdesc>& descs, hankel_dtype dtype,
                              uint32_t flags, int64_t* h_elems, int64_t* x_elems, int64_t* y_elems, int64_t* sum_L,
                              int64_t* max_L, std::string& err);
 hankel_status general_forward(GeneralPlan* g, const void* h, const void* x, void* y, void* alpha, cudaStream_t st,

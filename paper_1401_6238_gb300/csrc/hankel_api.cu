@@ -231,6 +231,22 @@ hankel_status validate(const hankel_desc& d, int64_t i, uint32_t flags, int64_t&
     return HANKEL_OK;
 }
 
+// A one- or two-level descriptor in the level-k form of the general path.
+hankel_mdesc to_levels(const hankel_desc& d, bool block) {
+    hankel_mdesc m;
+    std::memset(&m, 0, sizeof(m));
+    m.m = d.m;
+    m.levels = block ? 2 : 1;
+    for (int q = 0; q < d.m; ++q) {
+        m.n[0][q] = d.n[q];
+        m.n[1][q] = block ? d.N[q] : 1;
+    }
+    m.h_off = d.h_off;
+    for (int q = 0; q < HANKEL_MAX_ORDER; ++q) m.x_off[q] = d.x_off[q];
+    m.y_off = d.y_off;
+    return m;
+}
+
 // Per-pass twiddle tables (fft_stage.cuh layout) of every distinct length.
 hankel_status upload_twiddles(hankel_plan_s* p, const std::vector<int>& Ls) {
     int64_t total = 0;
@@ -499,9 +515,53 @@ hankel_status hankel_plan(hankel_plan_t* out, const hankel_desc* descs, int64_t 
         s = upload_twiddles(p, Ls);
         if (s == HANKEL_OK) s = build_real_path(p);
     } else {
-        s = hk::general_create(&p->gen, p->descs, dtype, flags, &p->h_elems, &p->x_elems, &p->y_elems,
-                               &p->sum_L, &p->max_L, g_err);
+        // the general path takes level-k descriptors: level 1 (Hankel) or,
+        // with HANKEL_BLOCK, level 2 (BHHB: block sizes n, block counts N)
+        std::vector<hankel_mdesc> md(p->descs.size());
+        for (size_t i = 0; i < p->descs.size(); ++i) md[i] = to_levels(p->descs[i], block);
+        s = hk::general_create(&p->gen, md, dtype, flags, &p->h_elems, &p->x_elems, &p->y_elems, &p->sum_L,
+                               &p->max_L, g_err);
     }
+    if (s != HANKEL_OK) { free_plan(p); return s; }
+    *out = p;
+    return HANKEL_OK;
+}
+
+hankel_status hankel_plan_multilevel(hankel_plan_t* out, const hankel_mdesc* descs, int64_t count, hankel_dtype dtype,
+                                     uint32_t flags) {
+    if (out == nullptr) return fail(HANKEL_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (descs == nullptr || count < 1) return fail(HANKEL_EINVAL, "need at least one descriptor");
+    if (dtype < HANKEL_R32 || dtype > HANKEL_C128) return fail(HANKEL_EINVAL, "unknown dtype %d", (int)dtype);
+    if (flags & ~(uint32_t)(HANKEL_SAME_X | HANKEL_STORE_SPECTRA))
+        return fail(HANKEL_EINVAL, "flags 0x%x: only HANKEL_SAME_X and HANKEL_STORE_SPECTRA apply", flags);
+    for (int64_t i = 0; i < count; ++i) {
+        const hankel_mdesc& d = descs[i];
+        if (d.m < 2 || d.m > HANKEL_MAX_ORDER)
+            return fail(HANKEL_EINVAL, "descriptor %lld: order m=%d outside [2, %d]", (long long)i, d.m,
+                        HANKEL_MAX_ORDER);
+        if (d.levels < 1 || d.levels > HANKEL_MAX_LEVELS)
+            return fail(HANKEL_EINVAL, "descriptor %lld: levels=%d outside [1, %d]", (long long)i, d.levels,
+                        HANKEL_MAX_LEVELS);
+        for (int l = 0; l < d.levels; ++l)
+            for (int q = 0; q < d.m; ++q)
+                if (d.n[l][q] < 1)
+                    return fail(HANKEL_EINVAL, "descriptor %lld: n[%d][%d]=%d must be >= 1", (long long)i, l, q,
+                                d.n[l][q]);
+        if (d.h_off < 0 || d.y_off < 0) return fail(HANKEL_EINVAL, "descriptor %lld: negative offset", (long long)i);
+        const int nx = (flags & HANKEL_SAME_X) ? 1 : d.m;
+        for (int q = 0; q < nx; ++q)
+            if (d.x_off[q] < 0) return fail(HANKEL_EINVAL, "descriptor %lld: negative x_off[%d]", (long long)i, q);
+    }
+    auto* p = new (std::nothrow) hankel_plan_s;
+    if (!p) return fail(HANKEL_ENOMEM, "host allocation failed");
+    p->dtype = dtype;
+    p->flags = flags | HANKEL_BLOCK;  // computes through hankel_txv_block
+    cudaGetDevice(&p->device);
+    std::vector<hankel_mdesc> md(descs, descs + count);
+    p->descs.resize(count);  // only the count is read back (hankel_plan_query, staging sizes)
+    hankel_status s = hk::general_create(&p->gen, md, dtype, flags, &p->h_elems, &p->x_elems, &p->y_elems,
+                                         &p->sum_L, &p->max_L, g_err);
     if (s != HANKEL_OK) { free_plan(p); return s; }
     *out = p;
     return HANKEL_OK;

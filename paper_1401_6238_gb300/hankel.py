@@ -3,6 +3,7 @@
 Argument marshalling only: every step of the products runs in the library's
 CUDA kernels.  The functions ``hankel_plan``, ``hankel_txv``,
 ``hankel_txv_host``, ``hankel_txv_block``, ``hankel_txv_backward``,
+``hankel_plan_multilevel``,
 ``hankel_plan_query``, ``hankel_plan_destroy`` and ``hankel_last_error``
 mirror the C entry points one to one; ``Plan`` and ``HankelTxV`` (a
 ``torch.autograd.Function``) are conveniences built on them.
@@ -30,6 +31,10 @@ STATUS_NAMES = {OK: "HANKEL_OK", EINVAL: "HANKEL_EINVAL", ENOMEM: "HANKEL_ENOMEM
 # Mirror of struct hankel_desc (natural C alignment).
 DESC_DTYPE = np.dtype([("m", np.int32), ("n", np.int32, (MAX_ORDER,)), ("N", np.int32, (MAX_ORDER,)),
                        ("h_off", np.int64), ("x_off", np.int64, (MAX_ORDER,)), ("y_off", np.int64)], align=True)
+# Mirror of struct hankel_mdesc (level-k block Hankel tensors).
+MAX_LEVELS = 4
+MDESC_DTYPE = np.dtype([("m", np.int32), ("levels", np.int32), ("n", np.int32, (MAX_LEVELS, MAX_ORDER)),
+                        ("h_off", np.int64), ("x_off", np.int64, (MAX_ORDER,)), ("y_off", np.int64)], align=True)
 
 
 class PlanInfo(ctypes.Structure):
@@ -54,6 +59,8 @@ _lib = None
 _SIGS = {
     "hankel_plan": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
                                    ctypes.c_uint32]),
+    "hankel_plan_multilevel": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_int64,
+                                              ctypes.c_int, ctypes.c_uint32]),
     "hankel_txv": (ctypes.c_int, [ctypes.c_void_p] * 6),
     "hankel_txv_host": (ctypes.c_int, [ctypes.c_void_p] * 6),
     "hankel_txv_block": (ctypes.c_int, [ctypes.c_void_p] * 6),
@@ -142,6 +149,14 @@ def hankel_plan(descs, dtype, flags=0):
     return h.value
 
 
+def hankel_plan_multilevel(descs, dtype, flags=0):
+    """Make a plan for level-k block Hankel tensors from an MDESC_DTYPE array."""
+    descs = np.ascontiguousarray(descs, dtype=MDESC_DTYPE)
+    h = ctypes.c_void_p()
+    _check(load().hankel_plan_multilevel(ctypes.byref(h), descs.ctypes.data, descs.shape[0], int(dtype), int(flags)))
+    return h.value
+
+
 def hankel_txv(plan, h, x, y, alpha, stream=None):
     _check(load().hankel_txv(plan, _ptr(h), _ptr(x), _ptr(y), _ptr(alpha), _stream(stream)))
 
@@ -210,6 +225,28 @@ def make_descs(count):
     return np.zeros(count, dtype=DESC_DTYPE)
 
 
+def make_mdescs(count):
+    return np.zeros(count, dtype=MDESC_DTYPE)
+
+
+def level_descs(sizes, h_offs, x_offs, y_offs):
+    """Level-k descriptors of tensors sharing one shape: ``sizes[l][p]`` is
+    the size of mode p+1 at level l+1; ``x_offs[t]`` lists the offsets of
+    x_1..x_m of tensor t."""
+    k, m = len(sizes), len(sizes[0])
+    count = len(h_offs)
+    d = make_mdescs(count)
+    d["m"] = m
+    d["levels"] = k
+    for l in range(k):
+        d["n"][:, l, :m] = sizes[l]
+    d["h_off"] = h_offs
+    for t in range(count):
+        d["x_off"][t, : len(x_offs[t])] = x_offs[t]
+    d["y_off"] = y_offs
+    return d
+
+
 def square_descs(orders, dims, h_off, x_off, y_off):
     """Descriptors of square tensors with one vector each (HANKEL_SAME_X)."""
     orders = np.asarray(orders)
@@ -239,7 +276,11 @@ class Plan:
     def __init__(self, descs, dtype, flags=0):
         self.dtype = int(dtype)
         self.flags = int(flags)
-        self.handle = hankel_plan(descs, dtype, flags)
+        if np.asarray(descs).dtype == MDESC_DTYPE:
+            self.handle = hankel_plan_multilevel(descs, dtype, flags)
+            self.flags |= BLOCK  # level-k plans compute through txv_block
+        else:
+            self.handle = hankel_plan(descs, dtype, flags)
         self.info = hankel_plan_query(self.handle)
 
     def torch_dtype(self):

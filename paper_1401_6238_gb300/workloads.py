@@ -21,6 +21,8 @@ products and its Section 4 exponential-data-fitting signals):
   exponentials with given poles, e.g. the 2-peak signal of Example 4.1.
 * ``unit_columns``   -- random complex unit-norm columns standing in for the
   HOOI factor columns of Section 4.2.
+* ``edf_3d_signal`` / ``random_arrays`` -- a 3D damped-exponential signal
+  (generating tensor of a level-3 block Hankel tensor) and random arrays.
 """
 
 from dataclasses import dataclass, field
@@ -230,3 +232,31 @@ def unit_matrices(count, n, N, seed=7):
     rng = np.random.default_rng(seed)
     X = rng.standard_normal((count, n, N)) + 1j * rng.standard_normal((count, n, N))
     return X / np.linalg.norm(X.reshape(count, -1), axis=1)[:, None, None]
+
+
+def edf_3d_signal(shape=(64, 64, 64), K=6, snr_db=20.0, seed=10):
+    """x_{n1 n2 n3} = sum_k c_k z_{1,k}^{n1} z_{2,k}^{n2} z_{3,k}^{n3} + noise:
+    the three-dimensional analogue of the Section 4.3 signal, generating
+    tensor of a level-3 block Hankel tensor (Section 2.2)."""
+    rng = np.random.default_rng(seed)
+    s = np.zeros(shape, dtype=np.complex128)
+    axes = [np.arange(n) for n in shape]
+    for _ in range(K):
+        c = rng.uniform(0.5, 2.0) * np.exp(1j * rng.uniform(-np.pi, np.pi))
+        term = np.asarray(c, dtype=np.complex128)
+        for ax, t in enumerate(axes):
+            z = np.exp(-rng.uniform(0.002, 0.03) + 1j * rng.uniform(-np.pi, np.pi))
+            sh = [1] * len(shape)
+            sh[ax] = shape[ax]
+            term = term * (z ** t).reshape(sh)
+        s += term
+    return s + _noise(rng, shape, s, snr_db)
+
+
+def random_arrays(count, shape, seed=11, complex_=True):
+    """``count`` random arrays of the given shape with unit Frobenius norm."""
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((count,) + tuple(shape))
+    if complex_:
+        X = X + 1j * rng.standard_normal((count,) + tuple(shape))
+    return X / np.linalg.norm(X.reshape(count, -1), axis=1).reshape((count,) + (1,) * len(shape))

@@ -127,3 +127,35 @@ def test_tuning_knobs(lib):
             assert e.value.status == hk.EINVAL
     finally:
         hk.hankel_set_tuning(*old)
+
+
+def test_mdesc_layout_matches_header():
+    # int32 m, int32 levels, int32 n[4][8], int64 h_off, int64 x_off[8], int64 y_off
+    assert hk.MDESC_DTYPE.itemsize == 216
+    assert hk.MDESC_DTYPE.fields["h_off"][1] == 136
+    assert hk.MDESC_DTYPE.fields["x_off"][1] == 144
+    assert hk.MDESC_DTYPE.fields["y_off"][1] == 208
+
+
+@pytest.mark.parametrize("mutate,msg", [
+    (lambda d: d.__setitem__("levels", 0), "levels"),
+    (lambda d: d.__setitem__("levels", 5), "levels"),
+    (lambda d: d.__setitem__("m", 1), "order"),
+    (lambda d: d["n"].__setitem__((0, 2, 1), 0), "n[2][1]"),
+    (lambda d: d.__setitem__("y_off", -3), "negative"),
+])
+def test_multilevel_validation(lib, mutate, msg):
+    d = hk.level_descs([[2, 3, 2], [2, 2, 1], [3, 1, 2]], [0], [[0, 10, 20]], [0])
+    mutate(d)
+    with pytest.raises(hk.HankelError) as e:
+        hk.hankel_plan_multilevel(d, hk.C64, 0)
+    assert e.value.status == hk.EINVAL
+    assert msg in e.value.message
+
+
+def test_multilevel_rejects_other_flags(lib):
+    d = hk.level_descs([[2, 3, 2], [2, 2, 1]], [0], [[0, 10, 20]], [0])
+    for bad in (hk.FP64_POWER, hk.ONE_PER_LAUNCH, hk.BLOCK, 1 << 9):
+        with pytest.raises(hk.HankelError) as e:
+            hk.hankel_plan_multilevel(d, hk.C64, bad)
+        assert e.value.status == hk.EINVAL

@@ -229,12 +229,15 @@ __device__ __forceinline__ int sp(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int smem_elems(int L) { return L + (L >> 4) + 1; }
 
 struct Group {
-    int tid, nthr, bar;  // bar 0: the whole block
+    int tid, nthr, bar;  // bar 0: the whole block; > 0: named barrier; < 0: lanes `mask` of one warp
+    unsigned mask = 0xffffffffu;
     __device__ __forceinline__ void sync() const {
         if (bar == 0) {
             __syncthreads();
-        } else {
+        } else if (bar > 0) {
             asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nthr) : "memory");
+        } else {
+            __syncwarp(mask);
         }
     }
 };

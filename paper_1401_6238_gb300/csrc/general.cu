@@ -84,12 +84,14 @@ struct AccTask {
     int32_t k, t0, t1;
     int32_t L[MAXLV];
     int64_t count, dst;
+    int32_t bfirst, nblk;  // blocks of the accumulate launch given to this task (by its work)
 };
 
 struct Launch {
     int kind;  // 0 line, 1 alpha, 2 accumulate
     int first, count, L;
     int role;  // ROLE_SPECTRUM: spectra, always run; ROLE_PRODUCT: only when y is wanted
+    int what;  // buffers of a run: 0 workspace source, 1 h operand, 2 x operand, 3 + sel output sink
 };
 
 template <typename T>
@@ -178,6 +180,54 @@ __global__ void __launch_bounds__(512) line_kernel(const LineTask* __restrict__ 
                  LineSink<T>{dbase, t.dst_len, t.dst_stride, t.dst_conj, t.dst_real & 1, (T)t.scale}, false, tw, g);
 }
 
+// Short lines, several per warp (lines of one launch share their length L):
+// a group of `gth` < 32 lanes transforms one line, synchronising with the
+// other groups of its warp (__syncwarp over the lanes that hold a line: the
+// groups of a warp run the same pass sequence), so a warp keeps 32 / gth
+// lines in flight instead of one line with mostly idle lanes.  The block
+// loads the twiddle table once.
+template <typename T>
+__global__ void __launch_bounds__(256) line_group_kernel(const LineTask* __restrict__ tasks, int first, int count,
+                                                         int lpb, int gth, const void* __restrict__ in, void* out,
+                                                         cx<T>* ws, const cx<T>* __restrict__ tw_all, int L) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T>* tws = reinterpret_cast<cx<T>*>(smem_raw + RED_BYTES);
+    cx<T>* bufs = tws + TWG_SMEM;
+    const int E = smem_elems(L);
+    int64_t* ops_all = reinterpret_cast<int64_t*>(bufs + (size_t)2 * lpb * E);
+    const int tid = threadIdx.x;
+    const int base = first + blockIdx.x * lpb;
+    const int nl = min(lpb, first + count - base);
+    const TwTab<T> tw = load_twiddles(tws, tw_all + tasks[base].P.tw_off, L, Group{tid, (int)blockDim.x, 0});
+    for (int w = tid; w < nl * MAXOPS; w += blockDim.x) ops_all[w] = tasks[base + w / MAXOPS].ops[w % MAXOPS];
+    __syncthreads();
+    const int j = tid / gth;
+    if (j >= nl) return;
+    // lanes of this warp that hold a line
+    const int lane = tid & 31, warp_first_line = (tid - lane) / gth;
+    const int lines_here = min(32 / gth, nl - warp_first_line);
+    const unsigned mask = (lines_here * gth >= 32) ? 0xffffffffu : ((1u << (lines_here * gth)) - 1u);
+    Group g{tid - j * gth, gth, -1};
+    g.mask = mask;
+    const LineTask& t = tasks[base + j];
+    cx<T>* b0 = bufs + (2 * j) * E;
+    cx<T>* b1 = b0 + E;
+    if (t.src_mode == SRC_OPERAND) {
+        const bool real = t.dst_real & 2;
+        const void* sbase = (const char*)in + t.src * (real ? sizeof(T) : sizeof(cx<T>));
+        const OperandLoad<T> ld{sbase, t.src_len, t.src_stride, t.src_conj, real ? 1 : 0};
+        for (int i = g.tid; i < L; i += g.nthr) b0[sp(i)] = ld(i);
+    } else {
+        const ProductLoad<T> ld{ws, ops_all + j * MAXOPS, t.nops, t.src_len, t.src_conj, t.loff, t.lstride};
+        for (int i = g.tid; i < L; i += g.nthr) b0[sp(i)] = ld(i);
+    }
+    g.sync();
+    void* dbase = (t.dst_buf == BUF_WS) ? (void*)(ws + t.dst)
+                                        : (void*)((char*)out + t.dst * ((t.dst_real & 1) ? sizeof(T) : sizeof(cx<T>)));
+    fft_stage<T>(t.P, GLd<T>{nullptr, 0, nullptr, 0}, b0, b1, b0,
+                 LineSink<T>{dbase, t.dst_len, t.dst_stride, t.dst_conj, t.dst_real & 1, (T)t.scale}, false, tw, g);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) alpha_kernel(const AlphaTask* __restrict__ tasks, int first,
                                                     const cx<T>* __restrict__ ws, void* alpha, int real) {
@@ -205,18 +255,29 @@ __global__ void __launch_bounds__(256) alpha_kernel(const AlphaTask* __restrict_
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) accumulate_kernel(const AccTask* __restrict__ tasks, int first,
+__global__ void __launch_bounds__(256) accumulate_kernel(const AccTask* __restrict__ tasks, int first, int ntasks,
                                                          const Term* __restrict__ terms, cx<T>* ws) {
-    const AccTask& t = tasks[first + blockIdx.y];
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < t.count;
-         e += (int64_t)gridDim.x * blockDim.x) {
+    // the task owning this block: the last one whose first block is <= blockIdx.x
+    int lo = first, hi = first + ntasks - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tasks[mid].bfirst <= (int)blockIdx.x)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const AccTask& t = tasks[lo];
+    const int n = (int)t.count;  // arrays hold fewer than 2^31 elements (checked at plan time)
+    const int b = (int)blockIdx.x - t.bfirst;
+    for (int e = b * blockDim.x + threadIdx.x; e < n; e += t.nblk * blockDim.x) {
         // offset of the coordinate-wise negation (-c) mod L
-        int64_t re = 0, rest = e, st = 1;
+        int re = 0, rest = e, st = 1;
         for (int l = 0; l < t.k; ++l) {
-            const int64_t c = rest % t.L[l];
-            rest /= t.L[l];
-            re += (c == 0 ? 0 : t.L[l] - c) * st;
-            st *= t.L[l];
+            const int L = t.L[l];
+            const int q = rest / L, c = rest - q * L;
+            rest = q;
+            re += (c == 0 ? 0 : L - c) * st;
+            st *= L;
         }
         cx<T> acc = mk<T>(T(0), T(0));
         for (int j = t.t0; j < t.t1; ++j) {
@@ -321,6 +382,7 @@ struct GeneralPlan {
     std::vector<AlphaTask> alphas;
     std::vector<Term> terms;
     std::vector<AccTask> accs;
+    int acc_blocks = 0;
     std::vector<Launch> fwd_prog, bwd_prog_spec, bwd_prog_rest;
     LineTask *d_fwd = nullptr, *d_bwd = nullptr;
     AlphaTask* d_alpha = nullptr;
@@ -356,7 +418,7 @@ using Phases = std::vector<std::vector<Launch>>;
 void add_launch(Phases& ph, int phase, int first, int count, int L, int role) {
     if (count == 0) return;
     if ((int)ph.size() <= phase) ph.resize(phase + 1);
-    ph[phase].push_back({0, first, count, L, role});
+    ph[phase].push_back({0, first, count, L, role, 0});
 }
 
 // Spectrum array of an operand whose data (extents rows[], column-major) is
@@ -501,6 +563,33 @@ void compact(std::vector<LineTask>& lines, std::vector<std::vector<Launch>*> pro
     lines.swap(out);
 }
 
+// Split every line launch into runs of tasks that read the same input
+// buffer and write the same output buffer (done once, at plan time).
+std::vector<Launch> split_runs(const std::vector<Launch>& prog, const std::vector<LineTask>& lines) {
+    auto cls = [](const LineTask& t) {
+        if (t.dst_buf == BUF_OUT && t.out_sel != 0) return 3 + t.out_sel;
+        if (t.src_mode == SRC_OPERAND) return t.src_conj ? 1 : 2;
+        return 0;
+    };
+    std::vector<Launch> out;
+    for (const Launch& l : prog) {
+        if (l.kind != 0) {
+            out.push_back(l);
+            out.back().what = 0;
+            continue;
+        }
+        int i = l.first;
+        while (i < l.first + l.count) {
+            const int what = cls(lines[i]);
+            int j = i + 1;
+            while (j < l.first + l.count && cls(lines[j]) == what) ++j;
+            out.push_back({0, i, j - i, l.L, l.role, what});
+            i = j;
+        }
+    }
+    return out;
+}
+
 hankel_status cuerr(cudaError_t e, const char* what, std::string& err) {
     err = std::string(what) + ": " + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? HANKEL_ENOMEM : HANKEL_ECUDA;
@@ -527,9 +616,41 @@ int nthr_for(int L) {
     return std::max(32, std::min(512, p));
 }
 
+// Lanes per line of the grouped kernel for length L: about one radix-16
+// butterfly per lane, at least 4; 32 or more means one line per block.
+int group_lanes(int L) {
+    int p = 4;
+    while (p < 32 && p * 16 < L) p <<= 1;
+    return p;
+}
+
+size_t group_smem(const GeneralPlan* g, int L, int lpb) {
+    return RED_BYTES + ((size_t)TWG_SMEM + (size_t)lpb * 2 * smem_elems_host(L)) * csize(g) +
+           (size_t)lpb * MAXOPS * sizeof(int64_t);
+}
+
 template <typename T>
 cudaError_t run_lines(GeneralPlan* g, const Launch& l, const LineTask* d_tasks, const void* in, void* out,
                       cudaStream_t st) {
+    const int gth = group_lanes(l.L);
+    if (gth < 32) {
+        int lpb = 256 / gth;
+        while (lpb > 32 / gth && group_smem(g, l.L, lpb) > 227 * 1024) lpb /= 2;
+        const size_t smem = group_smem(g, l.L, lpb);
+        static size_t granted_group[64] = {0};
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (smem > granted_group[dev & 63]) {
+            e = cudaFuncSetAttribute(line_group_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            granted_group[dev & 63] = smem;
+        }
+        const int blocks = (l.count + lpb - 1) / lpb;
+        line_group_kernel<T><<<blocks, lpb * gth, smem, st>>>(d_tasks, l.first, l.count, lpb, gth, in, out,
+                                                              (cx<T>*)g->d_ws, (const cx<T>*)g->d_tw, l.L);
+        return cudaGetLastError();
+    }
     const size_t smem = line_smem(g, l.L);
     // raise the limit only when needed (no attribute calls in steady state,
     // so the launches can be captured into CUDA graphs); per device
@@ -672,7 +793,7 @@ hankel_status build_programs(GeneralPlan* g, const std::vector<hankel_mdesc>& de
         flatten(spec, prog, cuts);
         flatten(prod, prog, cuts);
         compact(g->fwd_lines, {&prog});
-        g->fwd_prog = merge(prog, cuts);
+        g->fwd_prog = split_runs(merge(prog, cuts), g->fwd_lines);
     }
     for (size_t i = 0; i < g->ds.size(); ++i) {
         const auto& D = g->ds[i];
@@ -729,6 +850,12 @@ hankel_status build_programs(GeneralPlan* g, const std::vector<hankel_mdesc>& de
             g->terms.insert(g->terms.end(), tl.begin(), tl.end());
             a.t1 = (int)g->terms.size();
             a.dst = splane[o];
+            // blocks in proportion to the work (elements x terms), about 8
+            // element-terms per thread
+            const int64_t work = a.count * (a.t1 - a.t0);
+            a.nblk = (int)std::max<int64_t>(1, std::min<int64_t>(8192, (work + 2047) / 2048));
+            a.bfirst = g->acc_blocks;
+            g->acc_blocks += a.nblk;
             g->accs.push_back(a);
             // grad_G = ifftn(S) = conj(fftn(conj S)) / total; grad_X = conj(fftn(S)); both cropped
             const bool h = op.is_h;
@@ -740,12 +867,12 @@ hankel_status build_programs(GeneralPlan* g, const std::vector<hankel_mdesc>& de
         std::vector<int> spec_cuts, rest_cuts;
         flatten(bspec, spec_list, spec_cuts);
         flatten(gspec, rest, rest_cuts);
-        if (!g->accs.empty()) rest.push_back({2, 0, (int)g->accs.size(), 0, ROLE_PRODUCT});
+        if (!g->accs.empty()) rest.push_back({2, 0, (int)g->accs.size(), 0, ROLE_PRODUCT, 0});
         rest_cuts.push_back((int)rest.size());
         flatten(tails, rest, rest_cuts);
         compact(g->bwd_lines, {&spec_list, &rest});
-        g->bwd_prog_spec = merge(spec_list, spec_cuts);
-        g->bwd_prog_rest = merge(rest, rest_cuts);
+        g->bwd_prog_spec = split_runs(merge(spec_list, spec_cuts), g->bwd_lines);
+        g->bwd_prog_rest = split_runs(merge(rest, rest_cuts), g->bwd_lines);
     }
     return HANKEL_OK;
 }
@@ -793,34 +920,14 @@ hankel_status general_create(GeneralPlan** out, const std::vector<hankel_mdesc>&
 
 namespace {
 
-// Run the line launches of a program.  Launches reading input operands are
-// split into runs of generating-tensor operands (read from `h`, conjugated
-// on load) and vector operands (read from `x`).
+// Run a program whose launches were split at plan time (split_runs) into
+// runs reading one input buffer and writing one output buffer.
 template <typename Skip, typename Run>
-cudaError_t run_program(GeneralPlan* g, const std::vector<Launch>& prog, const std::vector<LineTask>& lines,
-                        Skip skip, Run run) {
-    for (const Launch& l : prog) {
+cudaError_t run_program(const std::vector<Launch>& runs, Skip skip, Run run) {
+    for (const Launch& l : runs) {
         if (skip(l)) continue;
-        if (l.kind != 0) {
-            cudaError_t e = run(l, 0);
-            if (e != cudaSuccess) return e;
-            continue;
-        }
-        int i = l.first;
-        while (i < l.first + l.count) {
-            int j = i + 1;
-            int what = 0;  // 0 workspace source, 1 h operand, 2 x operand, 3 + sel output sink
-            auto cls = [&](const LineTask& t) {
-                if (t.dst_buf == BUF_OUT && t.out_sel != 0) return 3 + t.out_sel;
-                if (t.src_mode == SRC_OPERAND) return t.src_conj ? 1 : 2;
-                return 0;
-            };
-            what = cls(lines[i]);
-            while (j < l.first + l.count && cls(lines[j]) == what) ++j;
-            cudaError_t e = run({0, i, j - i, l.L, l.role}, what);
-            if (e != cudaSuccess) return e;
-            i = j;
-        }
+        cudaError_t e = run(l, l.what);
+        if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
@@ -834,7 +941,7 @@ hankel_status general_forward(GeneralPlan* g, const void* h, const void* x, void
         return HANKEL_EINVAL;
     }
     cudaError_t e = run_program(
-        g, g->fwd_prog, g->fwd_lines, [&](const Launch& l) { return l.role == ROLE_PRODUCT && y == nullptr; },
+        g->fwd_prog, [&](const Launch& l) { return l.role == ROLE_PRODUCT && y == nullptr; },
         [&](const Launch& l, int what) {
             const void* in = (what == 1) ? h : x;
             return g->dbl ? run_lines<double>(g, l, g->d_fwd, in, y, st) : run_lines<float>(g, l, g->d_fwd, in, y, st);
@@ -865,21 +972,20 @@ hankel_status general_backward(GeneralPlan* g, const void* gy, const void* h, co
     cudaError_t e = cudaSuccess;
     if (!(g->flags & HANKEL_STORE_SPECTRA)) {
         e = run_program(
-            g, g->bwd_prog_spec, g->bwd_lines, [](const Launch&) { return false; },
+            g->bwd_prog_spec, [](const Launch&) { return false; },
             [&](const Launch& l, int what) { return lines(l, what == 1 ? h : x, nullptr); });
         if (e != cudaSuccess) return cuerr(e, "backward spectra launch", err);
     }
     e = run_program(
-        g, g->bwd_prog_rest, g->bwd_lines, [](const Launch&) { return false; },
+        g->bwd_prog_rest, [](const Launch&) { return false; },
         [&](const Launch& l, int what) -> cudaError_t {
-            if (l.kind == 2) {
-                dim3 grid(64, l.count);
+            if (l.kind == 2) {  // one launch over every accumulate task
                 if (g->dbl)
-                    accumulate_kernel<double><<<grid, 256, 0, st>>>(g->d_accs, l.first, g->d_terms,
-                                                                    (cx<double>*)g->d_ws);
+                    accumulate_kernel<double><<<g->acc_blocks, 256, 0, st>>>(g->d_accs, l.first, l.count, g->d_terms,
+                                                                             (cx<double>*)g->d_ws);
                 else
-                    accumulate_kernel<float><<<grid, 256, 0, st>>>(g->d_accs, l.first, g->d_terms,
-                                                                   (cx<float>*)g->d_ws);
+                    accumulate_kernel<float><<<g->acc_blocks, 256, 0, st>>>(g->d_accs, l.first, l.count, g->d_terms,
+                                                                            (cx<float>*)g->d_ws);
                 return cudaGetLastError();
             }
             if (what >= 3) {  // gradient stores: grad_h (sel 1) or grad_x (sel 2)

@@ -81,7 +81,17 @@ enum {
     HANKEL_BLOCK = 1u << 3,
     /* Plain path: one tensor per kernel launch, no pairing or batching
      * (the comparison baseline; meant for the FP64 dtypes). */
-    HANKEL_ONE_PER_LAUNCH = 1u << 4
+    HANKEL_ONE_PER_LAUNCH = 1u << 4,
+    /* Descriptors describe anti-circulant tensors (Section 2.1:
+     * C[i_1..i_m] = c[(i_1 + ... + i_m) mod n]), square with every mode of
+     * size n (for BHHB and level-k plans: per level, the block anti-circulant
+     * tensors of Section 2.2).  h holds the compressed generating vector c
+     * (length n; block plans: the compressed generating array, column-major)
+     * and the products of Section 3 run at FFT length exactly n (Theorem
+     * 2.1), so n must be one of this build's FFT lengths
+     * (hankel_fft_length(n) == n, a 2,3,5,7-smooth length), else
+     * HANKEL_EUNSUPPORTED.  y has n entries per level. */
+    HANKEL_ANTICIRCULANT = 1u << 5
 };
 
 /*
@@ -179,7 +189,8 @@ hankel_status hankel_plan(hankel_plan_t* out, const hankel_desc* descs, int64_t 
  *   alpha = <ifftn(G~), fftn(X~_1) .* ... .* fftn(X~_m)>,
  * every array zero-padded to L_1 x ... x L_k with L_l >= D_l.
  *   descs, count, dtype  as hankel_plan (descriptors copied).
- *   flags   HANKEL_SAME_X and HANKEL_STORE_SPECTRA; other bits are EINVAL.
+ *   flags   HANKEL_SAME_X, HANKEL_STORE_SPECTRA and HANKEL_ANTICIRCULANT;
+ *           other bits are EINVAL.
  * The plan computes through hankel_txv_block (forward), hankel_txv_host and
  * hankel_txv_backward (adjoint, the k-dimensional analogue of the BHHB
  * gradients); hankel_txv refuses it.  Synchronous.

@@ -710,15 +710,33 @@ hankel_status build_programs(GeneralPlan* g, const std::vector<hankel_mdesc>& de
         D.m = d.m;
         D.geo.k = d.levels;
         int gs[MAXLV];
+        const bool anti = (g->flags & HANKEL_ANTICIRCULANT) != 0;
         for (int l = 0; l < d.levels; ++l) {
             int64_t s = 0;
             for (int p = 0; p < d.m; ++p) s += d.n[l][p];
-            gs[l] = (int)(s - d.m + 1);
+            if (anti) {
+                // compressed generating data: n entries per level, transformed at length exactly n
+                for (int p = 1; p < d.m; ++p)
+                    if (d.n[l][p] != d.n[l][0]) {
+                        err = "descriptor " + std::to_string(i) + ": anti-circulant tensors are square";
+                        return HANKEL_EINVAL;
+                    }
+                if (l == 0 && d.n[0][0] < 2) {
+                    err = "descriptor " + std::to_string(i) + ": anti-circulant dimension must be >= 2";
+                    return HANKEL_EINVAL;
+                }
+                gs[l] = d.n[l][0];
+            } else {
+                gs[l] = (int)(s - d.m + 1);
+            }
             // level 0 is always transformed (length >= 2); a level with D_l = 1 is not
-            const int64_t L = (l > 0 && gs[l] == 1) ? 1 : hankel_fft_length(gs[l]);
+            const int64_t L = (l > 0 && gs[l] == 1) ? 1 : (anti ? (int64_t)gs[l] : hankel_fft_length(gs[l]));
             FftPlan probe;
             if (L < 0 || L > maxL || (L > 1 && !fft_factor((int)L, &probe))) {
-                err = "descriptor " + std::to_string(i) + ": FFT length beyond the supported maximum of this build";
+                err = "descriptor " + std::to_string(i) +
+                      (anti ? ": anti-circulant dimension " + std::to_string(gs[l]) +
+                                  " is not an FFT length of this build (2,3,5,7-smooth, within the maximum)"
+                            : std::string(": FFT length beyond the supported maximum of this build"));
                 return HANKEL_EUNSUPPORTED;
             }
             D.geo.L[l] = (int)L;

@@ -352,7 +352,7 @@ hankel_status build_real_path(hankel_plan_s* p) {
         }
     auto fill = [&](hk::RealJob& J, int64_t i, bool B) {
         const hankel_desc& d = p->descs[i];
-        const int dl = (int)(d.n[0] * (int64_t)d.m - d.m + 1);
+        const int dl = (p->flags & HANKEL_ANTICIRCULANT) ? d.n[0] : (int)(d.n[0] * (int64_t)d.m - d.m + 1);
         if (!B) {
             J.mA = d.m; J.nA = d.n[0]; J.dA = dl; J.iA = (int)i;
             J.hA = d.h_off; J.xA = d.x_off[0]; J.yA = d.y_off; J.wsA = ws_off[i];
@@ -473,7 +473,7 @@ hankel_status hankel_plan(hankel_plan_t* out, const hankel_desc* descs, int64_t 
     *out = nullptr;
     if (descs == nullptr || count < 1) return fail(HANKEL_EINVAL, "need at least one descriptor");
     if (dtype < HANKEL_R32 || dtype > HANKEL_C128) return fail(HANKEL_EINVAL, "unknown dtype %d", (int)dtype);
-    if (flags & ~(uint32_t)0x1F) return fail(HANKEL_EINVAL, "unknown flag bits 0x%x", flags);
+    if (flags & ~(uint32_t)0x3F) return fail(HANKEL_EINVAL, "unknown flag bits 0x%x", flags);
     auto* p = new (std::nothrow) hankel_plan_s;
     if (!p) return fail(HANKEL_ENOMEM, "host allocation failed");
     p->dtype = dtype;
@@ -489,8 +489,27 @@ hankel_status hankel_plan(hankel_plan_t* out, const hankel_desc* descs, int64_t 
         if (s != HANKEL_OK) { free_plan(p); return s; }
         const hankel_desc& D = descs[i];
         const int nx = (flags & HANKEL_SAME_X) ? 1 : D.m;
+        if (flags & HANKEL_ANTICIRCULANT) {
+            for (int q = 1; q < D.m; ++q)
+                if (D.n[q] != D.n[0] || (block && D.N[q] != D.N[0])) {
+                    free_plan(p);
+                    return fail(HANKEL_EINVAL, "descriptor %lld: anti-circulant tensors are square", (long long)i);
+                }
+            if (D.n[0] < 2) {
+                free_plan(p);
+                return fail(HANKEL_EINVAL, "descriptor %lld: anti-circulant dimension n=%d must be >= 2",
+                            (long long)i, D.n[0]);
+            }
+            d = D.n[0];  // the compressed generating vector has n entries
+            if (!block && (lengths().find((int)d) == nullptr || d > maxL)) {
+                free_plan(p);
+                return fail(HANKEL_EUNSUPPORTED, "descriptor %lld: anti-circulant dimension n=%lld is not an FFT "
+                            "length of this build (2,3,5,7-smooth, at most %lld)", (long long)i, (long long)d,
+                            (long long)maxL);
+            }
+        }
         if (!block) {
-            const LenInfo* li = lengths().pick(d);
+            const LenInfo* li = (flags & HANKEL_ANTICIRCULANT) ? lengths().find((int)d) : lengths().pick(d);
             if (!li || li->L > maxL) {
                 free_plan(p);
                 return fail(HANKEL_EUNSUPPORTED, "descriptor %lld: generating length d=%lld exceeds the maximum "
@@ -533,8 +552,9 @@ hankel_status hankel_plan_multilevel(hankel_plan_t* out, const hankel_mdesc* des
     *out = nullptr;
     if (descs == nullptr || count < 1) return fail(HANKEL_EINVAL, "need at least one descriptor");
     if (dtype < HANKEL_R32 || dtype > HANKEL_C128) return fail(HANKEL_EINVAL, "unknown dtype %d", (int)dtype);
-    if (flags & ~(uint32_t)(HANKEL_SAME_X | HANKEL_STORE_SPECTRA))
-        return fail(HANKEL_EINVAL, "flags 0x%x: only HANKEL_SAME_X and HANKEL_STORE_SPECTRA apply", flags);
+    if (flags & ~(uint32_t)(HANKEL_SAME_X | HANKEL_STORE_SPECTRA | HANKEL_ANTICIRCULANT))
+        return fail(HANKEL_EINVAL, "flags 0x%x: only HANKEL_SAME_X, HANKEL_STORE_SPECTRA and HANKEL_ANTICIRCULANT apply",
+                    flags);
     for (int64_t i = 0; i < count; ++i) {
         const hankel_mdesc& d = descs[i];
         if (d.m < 2 || d.m > HANKEL_MAX_ORDER)

@@ -23,7 +23,7 @@ MAX_ORDER = 8
 
 OK, EINVAL, ENOMEM, ECUDA, EUNSUPPORTED, ETIMEOUT = range(6)
 R32, C64, R64, C128 = range(4)
-SAME_X, FP64_POWER, STORE_SPECTRA, BLOCK, ONE_PER_LAUNCH = 1, 2, 4, 8, 16
+SAME_X, FP64_POWER, STORE_SPECTRA, BLOCK, ONE_PER_LAUNCH, ANTICIRCULANT = 1, 2, 4, 8, 16, 32
 
 STATUS_NAMES = {OK: "HANKEL_OK", EINVAL: "HANKEL_EINVAL", ENOMEM: "HANKEL_ENOMEM", ECUDA: "HANKEL_ECUDA",
                 EUNSUPPORTED: "HANKEL_EUNSUPPORTED", ETIMEOUT: "HANKEL_ETIMEOUT"}

@@ -159,3 +159,16 @@ def test_multilevel_rejects_other_flags(lib):
         with pytest.raises(hk.HankelError) as e:
             hk.hankel_plan_multilevel(d, hk.C64, bad)
         assert e.value.status == hk.EINVAL
+
+
+def test_anticirculant_needs_square_tensors_and_fft_lengths(lib):
+    d = hk.square_descs([3], [11], [0], [0], [0])  # 11 is prime: no transform of that length
+    with pytest.raises(hk.HankelError) as e:
+        hk.hankel_plan(d, hk.R32, hk.SAME_X | hk.ANTICIRCULANT)
+    assert e.value.status == hk.EUNSUPPORTED and "n=11" in e.value.message
+    d = hk.make_descs(1)
+    d["m"] = 3
+    d["n"][0, :3] = [8, 8, 6]
+    with pytest.raises(hk.HankelError) as e:
+        hk.hankel_plan(d, hk.C64, hk.ANTICIRCULANT)
+    assert e.value.status == hk.EINVAL and "square" in e.value.message

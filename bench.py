@@ -248,6 +248,28 @@ def secondary_workloads(dev, stream, steps=10, warmup=3):
                    "value": count / ((ms_f + ms_b) / 1e3), "unit": "forward+adjoint products/s",
                    "forward_ms": ms_f, "adjoint_ms": ms_b}
     plan.close()
+    # distinct vectors per mode (Section 3's m + 1 transform form): the
+    # 8192-tensor batch shape with x_1 .. x_m per tensor, FP32
+    bd, xoffs = wl.batched_distinct(8192, seed=12)
+    dd = hk.make_descs(len(bd))
+    dd["m"] = bd.orders
+    for p in range(hk.MAX_ORDER):
+        dd["n"][:, p] = np.where(p < bd.orders, bd.dims, 0)
+    dd["h_off"] = bd.h_off
+    for i, offs in enumerate(xoffs):
+        dd["x_off"][i, :len(offs)] = offs
+    dd["y_off"] = bd.y_off
+    plan = hk.Plan(dd, hk.R32, 0)
+    Hd, Xd = f32(bd.h), f32(bd.x)
+    Yd = torch.zeros(bd.y_len, dtype=torch.float32, device=dev)
+    Ad = torch.zeros(len(bd), dtype=torch.float32, device=dev)
+    ms_y = timed(lambda: plan.txv(Hd, Xd, Yd, None, stream), steps, warmup, stream)
+    ms_ya = timed(lambda: plan.txv(Hd, Xd, Yd, Ad, stream), steps, warmup, stream)
+    out["distinct"] = {"workload": "8192 real tensors, m in {3,4,5}, n in [16,1024], a different unit-norm vector "
+                                   "in every mode, FP32; y = H x_2 ... x_m, and with alpha = H x_1 ... x_m",
+                       "value": len(bd) / (ms_y / 1e3), "unit": "products/s", "y_ms": ms_y, "y_and_alpha_ms": ms_ya,
+                       "jobs": plan.info["jobs"], "launches": plan.info["launches"]}
+    plan.close()
     # level-3 block Hankel products (Section 2.2): a 64^3 3D signal as
     # generating tensor, sizes (22,22,22) at every level, 32 vector triples
     count, n3 = 32, 22 ** 3

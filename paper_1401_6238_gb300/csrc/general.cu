@@ -520,16 +520,46 @@ void emit_crop_transform(GeneralPlan* g, const Geo& geo, const std::vector<int64
     }
 }
 
+// Threads per block of a one-line launch of length L.
+int nthr_for(int L) {
+    int p = 1;
+    while (p < (L + 15) / 16) p <<= 1;
+    return std::max(32, std::min(512, p));
+}
+
+// Buffers a line task reads and writes: 0 workspace source, 1 h operand,
+// 2 x operand, 3 + sel an output sink (grad_h / grad_x).
+int task_class(const LineTask& t) {
+    if (t.dst_buf == BUF_OUT && t.out_sel != 0) return 3 + t.out_sel;
+    if (t.src_mode == SRC_OPERAND) return t.src_conj ? 1 : 2;
+    return 0;
+}
+
+// Lines that may share a launch: one length each up to 256 (several lines
+// per warp need one pass sequence), above that every length with the same
+// block size (one line per block, shared memory sized for the longest).
+int len_bucket(int L) { return L <= 256 ? L : (1 << 20) + nthr_for(L); }
+
 // Flatten phases into one program; `cuts` receives the phase boundaries.
-void flatten(const Phases& ph, std::vector<Launch>& prog, std::vector<int>& cuts) {
-    for (const auto& p : ph) {
+// Inside a phase (independent tasks) launches are ordered by the buffers
+// they use and by length bucket, so that merge() can join them.
+void flatten(const Phases& ph, std::vector<Launch>& prog, std::vector<int>& cuts, const std::vector<LineTask>& lines) {
+    for (auto p : ph) {
+        std::stable_sort(p.begin(), p.end(), [&](const Launch& a, const Launch& b) {
+            const int ca = a.kind == 0 ? task_class(lines[a.first]) : -1;
+            const int cb = b.kind == 0 ? task_class(lines[b.first]) : -1;
+            if (ca != cb) return ca < cb;
+            if (len_bucket(a.L) != len_bucket(b.L)) return len_bucket(a.L) < len_bucket(b.L);
+            return a.L > b.L;
+        });
         prog.insert(prog.end(), p.begin(), p.end());
         cuts.push_back((int)prog.size());
     }
 }
 
-// Group consecutive launches of the same kind, length and role (independent
-// tasks of one phase) to cut launch counts.
+// Group consecutive launches of the same kind, length bucket and role
+// (independent tasks of one phase) to cut launch counts; a merged launch
+// carries the longest length.
 std::vector<Launch> merge(const std::vector<Launch>& in, const std::vector<int>& barriers) {
     std::vector<Launch> out;
     size_t bi = 0;
@@ -539,11 +569,13 @@ std::vector<Launch> merge(const std::vector<Launch>& in, const std::vector<int>&
             if (barriers[bi] == (int)i) cut = true;
             ++bi;
         }
-        if (!out.empty() && !cut && out.back().kind == in[i].kind && out.back().L == in[i].L &&
-            out.back().role == in[i].role && out.back().first + out.back().count == in[i].first)
+        if (!out.empty() && !cut && out.back().kind == in[i].kind && len_bucket(out.back().L) == len_bucket(in[i].L) &&
+            out.back().role == in[i].role && out.back().first + out.back().count == in[i].first) {
             out.back().count += in[i].count;
-        else
+            out.back().L = std::max(out.back().L, in[i].L);
+        } else {
             out.push_back(in[i]);
+        }
     }
     return out;
 }
@@ -566,11 +598,7 @@ void compact(std::vector<LineTask>& lines, std::vector<std::vector<Launch>*> pro
 // Split every line launch into runs of tasks that read the same input
 // buffer and write the same output buffer (done once, at plan time).
 std::vector<Launch> split_runs(const std::vector<Launch>& prog, const std::vector<LineTask>& lines) {
-    auto cls = [](const LineTask& t) {
-        if (t.dst_buf == BUF_OUT && t.out_sel != 0) return 3 + t.out_sel;
-        if (t.src_mode == SRC_OPERAND) return t.src_conj ? 1 : 2;
-        return 0;
-    };
+    const auto cls = task_class;
     std::vector<Launch> out;
     for (const Launch& l : prog) {
         if (l.kind != 0) {
@@ -608,12 +636,6 @@ hankel_status upload(const std::vector<V>& v, V** d, std::string& err) {
 
 size_t line_smem(const GeneralPlan* g, int L) {
     return RED_BYTES + ((size_t)TWG_SMEM + 2 * smem_elems_host(L)) * csize(g);
-}
-
-int nthr_for(int L) {
-    int p = 1;
-    while (p < (L + 15) / 16) p <<= 1;
-    return std::max(32, std::min(512, p));
 }
 
 // Lanes per line of the grouped kernel for length L: about one radix-16
@@ -808,8 +830,8 @@ hankel_status build_programs(GeneralPlan* g, const std::vector<hankel_mdesc>& de
         }
         std::vector<Launch> prog;
         std::vector<int> cuts;
-        flatten(spec, prog, cuts);
-        flatten(prod, prog, cuts);
+        flatten(spec, prog, cuts, g->fwd_lines);
+        flatten(prod, prog, cuts, g->fwd_lines);
         compact(g->fwd_lines, {&prog});
         g->fwd_prog = split_runs(merge(prog, cuts), g->fwd_lines);
     }
@@ -883,11 +905,11 @@ hankel_status build_programs(GeneralPlan* g, const std::vector<hankel_mdesc>& de
         }
         std::vector<Launch> spec_list, rest;
         std::vector<int> spec_cuts, rest_cuts;
-        flatten(bspec, spec_list, spec_cuts);
-        flatten(gspec, rest, rest_cuts);
+        flatten(bspec, spec_list, spec_cuts, g->bwd_lines);
+        flatten(gspec, rest, rest_cuts, g->bwd_lines);
         if (!g->accs.empty()) rest.push_back({2, 0, (int)g->accs.size(), 0, ROLE_PRODUCT, 0});
         rest_cuts.push_back((int)rest.size());
-        flatten(tails, rest, rest_cuts);
+        flatten(tails, rest, rest_cuts, g->bwd_lines);
         compact(g->bwd_lines, {&spec_list, &rest});
         g->bwd_prog_spec = split_runs(merge(spec_list, spec_cuts), g->bwd_lines);
         g->bwd_prog_rest = split_runs(merge(rest, rest_cuts), g->bwd_lines);

@@ -173,6 +173,11 @@ struct hankel_plan_s {
     std::vector<hankel_desc> descs;
     std::vector<int> Lof;
     bool real_path = false;
+    // fused path for real tensors with a different vector per mode
+    bool multi_path = false;
+    std::vector<hk::MultiJob> multi_jobs;
+    std::vector<hk::RealLaunch> multi_launches;
+    hk::MultiJob* d_multi = nullptr;
     // fused real path
     std::vector<hk::RealJob> fwd_jobs, bwd_jobs;
     std::vector<hk::RealLaunch> fwd_launches, bwd_launches;
@@ -200,6 +205,7 @@ void free_plan(hankel_plan_s* p) {
     if (!p) return;
     cudaFree(p->d_fwd);
     cudaFree(p->d_bwd);
+    cudaFree(p->d_multi);
     cudaFree(p->d_tw);
     cudaFree(p->d_ws);
     cudaFree(p->s_h);
@@ -330,6 +336,27 @@ hk::FftPlan fft_plan_of(const hankel_plan_s* p, int L) {
     return P;
 }
 
+// Streams (at most 8) that the independent launches of one call fork onto,
+// with the fork/join events.
+hankel_status make_streams(hankel_plan_s* p, size_t nlaunch) {
+    const size_t nstreams = std::min<size_t>(8, nlaunch);
+    if (nstreams < 2) return HANKEL_OK;
+    cudaError_t e;
+    for (size_t i = 0; i < nstreams; ++i) {
+        cudaStream_t st;
+        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+        p->streams.push_back(st);
+    }
+    for (size_t i = 0; i <= nstreams; ++i) {
+        cudaEvent_t ev;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+        p->events.push_back(ev);
+    }
+    return HANKEL_OK;
+}
+
 hankel_status build_real_path(hankel_plan_s* p) {
     const int64_t count = (int64_t)p->descs.size();
     const bool dbl = is_double(p->dtype);
@@ -416,21 +443,8 @@ hankel_status build_real_path(hankel_plan_s* p) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(jobs)");
     e = cudaMemcpy(p->d_bwd, p->bwd_jobs.data(), p->bwd_jobs.size() * jb, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(jobs)");
-    const size_t nstreams = opl ? 0 : std::min<size_t>(8, std::max(p->fwd_launches.size(), p->bwd_launches.size()));
-    if (nstreams > 1) {
-        for (size_t i = 0; i < nstreams; ++i) {
-            cudaStream_t st;
-            e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
-            p->streams.push_back(st);
-        }
-        for (size_t i = 0; i <= nstreams; ++i) {
-            cudaEvent_t ev;
-            e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
-            p->events.push_back(ev);
-        }
-    }
+    const hankel_status ss = make_streams(p, opl ? 0 : std::max(p->fwd_launches.size(), p->bwd_launches.size()));
+    if (ss != HANKEL_OK) return ss;
     p->ws_bytes = (size_t)std::max<int64_t>(ws, 1) * 2 * real_size(p->dtype);
     e = cudaMalloc(&p->d_ws, p->ws_bytes);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(workspace)");
@@ -461,6 +475,80 @@ hankel_status run_forked(hankel_plan_s* p, const std::vector<hk::RealLaunch>& la
             return cuda_fail(e, "cudaStreamWaitEvent");
     }
     return HANKEL_OK;
+}
+
+// Real tensors with distinct mode vectors: pair tensors of equal FFT length
+// (MultiJob), group pairs into launches by block size.
+hankel_status build_multi_path(hankel_plan_s* p) {
+    const int64_t count = (int64_t)p->descs.size();
+    std::vector<int64_t> order(count);
+    for (int64_t i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return p->Lof[a] > p->Lof[b]; });
+    auto fill = [&](hk::MultiJob& J, int64_t i, bool B) {
+        const hankel_desc& d = p->descs[i];
+        int64_t sn = 0;
+        for (int q = 0; q < d.m; ++q) sn += d.n[q];
+        const int dl = (p->flags & HANKEL_ANTICIRCULANT) ? d.n[0] : (int)(sn - d.m + 1);
+        if (!B) {
+            J.mA = d.m; J.iA = (int)i; J.dA = dl; J.hA = d.h_off; J.yA = d.y_off;
+            for (int q = 0; q < d.m; ++q) { J.nA[q] = d.n[q]; J.xA[q] = d.x_off[q]; }
+        } else {
+            J.mB = d.m; J.iB = (int)i; J.dB = dl; J.hB = d.h_off; J.yB = d.y_off;
+            for (int q = 0; q < d.m; ++q) { J.nB[q] = d.n[q]; J.xB[q] = d.x_off[q]; }
+        }
+    };
+    p->multi_jobs.clear();
+    for (size_t k = 0; k < order.size();) {
+        hk::MultiJob J;
+        std::memset(&J, 0, sizeof(J));
+        J.P = fft_plan_of(p, p->Lof[order[k]]);
+        fill(J, order[k], false);
+        J.iB = -1;
+        if (k + 1 < order.size() && p->Lof[order[k + 1]] == p->Lof[order[k]]) {
+            fill(J, order[k + 1], true);
+            k += 2;
+        } else {
+            k += 1;
+        }
+        p->multi_jobs.push_back(J);
+    }
+    // launches: consecutive jobs (lengths descending) with one block size
+    const bool opl = (p->flags & HANKEL_ONE_PER_LAUNCH) != 0;
+    p->multi_launches.clear();
+    for (size_t i = 0; i < p->multi_jobs.size();) {
+        hk::RealLaunch lc;
+        lc.first = (int)i;
+        lc.nthr = nthr_of(p->multi_jobs[i].P.L);
+        lc.emax = 0;
+        lc.Lmax = p->multi_jobs[i].P.L;
+        lc.arrays = 3;
+        size_t j = i + 1;
+        if (!opl)
+            while (j < p->multi_jobs.size() && nthr_of(p->multi_jobs[j].P.L) == lc.nthr) ++j;
+        lc.count = (int)(j - i);
+        p->multi_launches.push_back(lc);
+        i = j;
+    }
+    for (const auto& lc : p->multi_launches)
+        if (hk::real_launch_smem(is_double(p->dtype), lc) > kSmemLimit)
+            return fail(HANKEL_EUNSUPPORTED, "FFT length %d needs more shared memory than a block has", lc.Lmax);
+    const size_t jb = sizeof(hk::MultiJob);
+    cudaError_t e = cudaMalloc(&p->d_multi, std::max<size_t>(p->multi_jobs.size(), 1) * jb);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(jobs)");
+    e = cudaMemcpy(p->d_multi, p->multi_jobs.data(), p->multi_jobs.size() * jb, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(jobs)");
+    return make_streams(p, opl ? 0 : p->multi_launches.size());
+}
+
+// The general-path program of a plan (made on first use for plans whose
+// forward products run on a fused path but whose adjoint runs here).
+hankel_status ensure_general(hankel_plan_s* p) {
+    if (p->gen) return HANKEL_OK;
+    const bool block = (p->flags & HANKEL_BLOCK) != 0;
+    std::vector<hankel_mdesc> md(p->descs.size());
+    for (size_t i = 0; i < p->descs.size(); ++i) md[i] = to_levels(p->descs[i], block);
+    int64_t he, xe, ye, sl, ml;
+    return hk::general_create(&p->gen, md, p->dtype, p->flags, &he, &xe, &ye, &sl, &ml, g_err);
 }
 
 }  // namespace
@@ -529,8 +617,15 @@ hankel_status hankel_plan(hankel_plan_t* out, const hankel_desc* descs, int64_t 
         for (auto& D : p->descs)
             for (int q = 1; q < D.m; ++q) square = square && D.n[q] == D.n[0];
     p->real_path = !block && !is_complex(dtype) && (flags & HANKEL_SAME_X) && square;
+    // real tensors with a vector per mode: the fused m + 1 transform kernel
+    // when every length fits its three shared buffers
+    p->multi_path = !block && !is_complex(dtype) && !(flags & (HANKEL_SAME_X | HANKEL_STORE_SPECTRA)) &&
+                    p->max_L <= max_len_for(3, 2 * real_size(dtype));
     hankel_status s = HANKEL_OK;
-    if (p->real_path) {
+    if (p->multi_path) {
+        s = upload_twiddles(p, Ls);
+        if (s == HANKEL_OK) s = build_multi_path(p);
+    } else if (p->real_path) {
         s = upload_twiddles(p, Ls);
         if (s == HANKEL_OK) s = build_real_path(p);
     } else {
@@ -593,8 +688,12 @@ hankel_status hankel_txv(hankel_plan_t p, const void* h, const void* x, void* y,
     if (!h || !x) return fail(HANKEL_EINVAL, "h and x must be device pointers");
     if (!y && !alpha) return fail(HANKEL_EINVAL, "nothing to compute: y and alpha are both NULL");
     cudaStream_t st = (cudaStream_t)stream;
-    if (!p->real_path) return hk::general_forward(p->gen, h, x, y, alpha, st, g_err);
     const bool dbl = is_double(p->dtype);
+    if (p->multi_path)
+        return run_forked(p, p->multi_launches, st, [&](const hk::RealLaunch& lc, cudaStream_t s) {
+            return hk::launch_real_multi(dbl, lc, p->d_multi, h, x, y, alpha, p->d_tw, s);
+        });
+    if (!p->real_path) return hk::general_forward(p->gen, h, x, y, alpha, st, g_err);
     return run_forked(p, p->fwd_launches, st, [&](const hk::RealLaunch& lc, cudaStream_t s) {
         return hk::launch_real_forward(dbl, lc, p->d_fwd, h, x, y, alpha, p->d_tw, p->d_ws, (int)p->flags, s);
     });
@@ -647,6 +746,11 @@ hankel_status hankel_txv_backward(hankel_plan_t p, const void* grad_y, const voi
     if (!grad_y || !h || !x) return fail(HANKEL_EINVAL, "grad_y, h and x must be device pointers");
     if (!grad_h && !grad_x) return fail(HANKEL_EINVAL, "nothing to compute: grad_h and grad_x are both NULL");
     cudaStream_t st = (cudaStream_t)stream;
+    if (p->multi_path) {
+        // the adjoint of the distinct-vector products runs on the general path
+        const hankel_status s = ensure_general(p);
+        if (s != HANKEL_OK) return s;
+    }
     if (!p->real_path) return hk::general_backward(p->gen, grad_y, h, x, grad_h, grad_x, st, g_err);
     const bool dbl = is_double(p->dtype);
     const int stored = (p->flags & HANKEL_STORE_SPECTRA) ? 1 : 0;
@@ -665,7 +769,12 @@ hankel_status hankel_plan_query(hankel_plan_t p, hankel_plan_info* info) {
     info->h_elems = p->h_elems;
     info->x_elems = p->x_elems;
     info->y_elems = p->y_elems;
-    if (p->real_path) {
+    if (p->multi_path) {
+        info->jobs = (int64_t)p->multi_jobs.size();
+        info->launches = (int64_t)p->multi_launches.size();
+        info->distinct_lengths = (int64_t)p->tw_off.size();
+        info->workspace_bytes = 0;
+    } else if (p->real_path) {
         info->jobs = (int64_t)p->fwd_jobs.size();
         info->launches = (int64_t)p->fwd_launches.size();
         info->distinct_lengths = (int64_t)p->tw_off.size();

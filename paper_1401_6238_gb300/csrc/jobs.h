@@ -38,6 +38,20 @@ struct RealJob {
     int64_t wsA, wsB;  // element offsets of each tensor's spectrum in the workspace
 };
 
+// Real tensors with a different vector in every mode (y = H x_2 ... x_m,
+// alpha = H x_1 ... x_m): a pair (A, B) of tensors with the same FFT length
+// shares every complex transform -- h_A + i h_B, then x_{A,p} + i x_{B,p}
+// mode by mode -- so a pair costs m + 1 transforms (Section 3's count for one
+// product).  iB < 0: tensor A alone.
+struct MultiJob {
+    FftPlan P;
+    int32_t mA, mB, iA, iB;
+    int32_t dA, dB;
+    int32_t nA[HANKEL_MAX_ORDER], nB[HANKEL_MAX_ORDER];
+    int64_t hA, hB, yA, yB;
+    int64_t xA[HANKEL_MAX_ORDER], xB[HANKEL_MAX_ORDER];
+};
+
 // Launch of one group of jobs that share a block size.
 struct RealLaunch {
     int32_t first, count;  // range in the job table

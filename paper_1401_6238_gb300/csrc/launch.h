@@ -22,6 +22,8 @@ cudaError_t launch_real_forward(bool dbl, const RealLaunch& lc, const RealJob* j
 cudaError_t launch_real_backward(bool dbl, const RealLaunch& lc, const RealJob* jobs, const void* gy, const void* h,
                                  const void* x, void* gh, void* gx, const void* tw, void* ws, int flags, int stored,
                                  cudaStream_t st);
+cudaError_t launch_real_multi(bool dbl, const RealLaunch& lc, const MultiJob* jobs, const void* h, const void* x,
+                              void* y, void* alpha, const void* tw, cudaStream_t st);
 cudaError_t launch_twiddles(bool dbl, void* out, int L, cudaStream_t st);
 // per-pass twiddle layout of fft_stage.cuh (real-data kernels)
 cudaError_t launch_stage_twiddles(bool dbl, void* out, const FftPlan& P, cudaStream_t st);

@@ -1,6 +1,8 @@
-// real_path.cu -- fused kernels for real square Hankel tensors with one
-// vector per tensor: y = H x^{m-1} and alpha = H x^m (Section 2.1 notation,
-// Section 3 procedures) and their adjoints.
+// real_path.cu -- fused kernels for real Hankel tensors: square tensors with
+// one vector per tensor, y = H x^{m-1} and alpha = H x^m (Section 2.1
+// notation, Section 3 procedures) and their adjoints, and tensors with a
+// different vector in every mode (real_multi_kernel, the m + 1 transform
+// form of Section 3).
 //
 // Forward, pair job (tensors A, B with the same FFT length L):
 //   S1 = fft(h~_A + i h~_B), S2 = fft(x~_A + i x~_B)      (zero-pad on load)
@@ -198,6 +200,112 @@ __global__ void __launch_bounds__(512) real_fwd_kernel(const RealJob* __restrict
         if (g.tid == 0) {
             alpha[J.iA] = (T)sA;
             if (!J.single && J.iB >= 0) alpha[J.iB] = (T)sB;
+        }
+    }
+}
+
+// Pair of real tensors with distinct mode vectors (MultiJob).  acc holds the
+// running spectral products P_A = ifft(h~_A) X_{A,2} ... and P_B for the
+// bins k = 0..L/2 (the rest follow by Hermitian symmetry): P_A at slot k,
+// P_B at slot L - k; at the self-paired bins 0 and L/2 both are real and
+// share one slot (real part A, imaginary part B).
+template <typename T>
+__global__ void __launch_bounds__(512) real_multi_kernel(const MultiJob* __restrict__ jobs, int first,
+                                                          const T* __restrict__ h, const T* __restrict__ x,
+                                                          T* __restrict__ y, T* __restrict__ alpha,
+                                                          const cx<T>* __restrict__ tw_all, int Lmax) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* red = reinterpret_cast<double*>(smem_raw);
+    cx<T>* tws = reinterpret_cast<cx<T>*>(smem_raw + RED_BYTES);
+    cx<T>* bA = tws + TW_SMEM;
+    cx<T>* bB = bA + smem_elems(Lmax);
+    cx<T>* acc = bB + smem_elems(Lmax);
+    const MultiJob& J = jobs[first + blockIdx.x];
+    const Group g{(int)threadIdx.x, (int)blockDim.x, 0};
+    const FftPlan P = J.P;
+    const int L = P.L;
+    const TwTab<T> tw = load_twiddles(tws, tw_all + P.tw_off, L, g);
+    const bool two = J.iB >= 0;
+    const int mA = J.mA, mB = two ? J.mB : 0;
+    const T invL = T(1) / T(L);
+    const PairSt<T> keep_st{nullptr, 0, nullptr, 0};
+    g.sync();
+    // ifft(h~) = conj(fft(h~)) / L for both tensors
+    cx<T>* S = fft_stage<T>(P, GLd<T>{h + J.hA, J.dA, two ? h + J.hB : nullptr, two ? J.dB : 0}, nullptr, bA, bB,
+                            keep_st, true, tw, g);
+    for (int k = g.tid; k <= L / 2; k += g.nthr) {
+        const int kc = (k == 0) ? 0 : L - k;
+        cx<T> HA, HB;
+        unpack(S[sp(k)], conjg(S[sp(kc)]), HA, HB);
+        if (kc == k) {
+            acc[sp(k)] = mk<T>(HA.x * invL, HB.x * invL);
+        } else {
+            acc[sp(k)] = scal(conjg(HA), invL);
+            acc[sp(kc)] = scal(conjg(HB), invL);
+        }
+    }
+    g.sync();
+    // modes 2..m: one transform of x_{A,p} + i x_{B,p} each, multiplied in
+    const int mmax = max(mA, mB);
+    for (int p = 1; p < mmax; ++p) {
+        const bool inA = p < mA, inB = p < mB;
+        S = fft_stage<T>(P, GLd<T>{inA ? x + J.xA[p] : nullptr, inA ? J.nA[p] : 0, inB ? x + J.xB[p] : nullptr,
+                                   inB ? J.nB[p] : 0},
+                         nullptr, bA, bB, keep_st, true, tw, g);
+        for (int k = g.tid; k <= L / 2; k += g.nthr) {
+            const int kc = (k == 0) ? 0 : L - k;
+            cx<T> XA, XB;
+            unpack(S[sp(k)], conjg(S[sp(kc)]), XA, XB);
+            if (kc == k) {
+                const cx<T> v = acc[sp(k)];
+                acc[sp(k)] = mk<T>(inA ? v.x * XA.x : v.x, inB ? v.y * XB.x : v.y);
+            } else {
+                if (inA) acc[sp(k)] = cmul(acc[sp(k)], XA);
+                if (inB) acc[sp(kc)] = cmul(acc[sp(kc)], XB);
+            }
+        }
+        g.sync();
+    }
+    if (y != nullptr) {
+        // Q = P_A + i P_B on all L bins; fft(Q) = y_A + i y_B (both real)
+        for (int k = g.tid; k <= L / 2; k += g.nthr) {
+            const int kc = (k == 0) ? 0 : L - k;
+            if (kc == k) {
+                bA[sp(k)] = acc[sp(k)];
+            } else {
+                const cx<T> PA = acc[sp(k)], PB = acc[sp(kc)];
+                bA[sp(k)] = PA + mul_pi(PB);
+                bA[sp(kc)] = conjg(PA) + mul_pi(conjg(PB));
+            }
+        }
+        g.sync();
+        fft_stage<T>(P, GLd<T>{nullptr, 0, nullptr, 0}, bA, bB, bA,
+                     PairSt<T>{y + J.yA, J.nA[0], two ? y + J.yB : nullptr, two ? J.nB[0] : 0}, false, tw, g);
+    }
+    if (alpha != nullptr) {
+        // alpha = sum_k P_k X_{1,k}: bins k and L - k contribute complex conjugates
+        S = fft_stage<T>(P, GLd<T>{x + J.xA[0], J.nA[0], two ? x + J.xB[0] : nullptr, two ? J.nB[0] : 0}, nullptr,
+                         bA, bB, keep_st, true, tw, g);
+        double aA = 0.0, aB = 0.0;
+        for (int k = g.tid; k <= L / 2; k += g.nthr) {
+            const int kc = (k == 0) ? 0 : L - k;
+            cx<T> XA, XB;
+            unpack(S[sp(k)], conjg(S[sp(kc)]), XA, XB);
+            if (kc == k) {
+                const cx<T> v = acc[sp(k)];
+                aA += (double)v.x * (double)XA.x;
+                aB += (double)v.y * (double)XB.x;
+            } else {
+                const cx<T> PA = acc[sp(k)], PB = acc[sp(kc)];
+                aA += 2.0 * ((double)PA.x * XA.x - (double)PA.y * XA.y);
+                aB += 2.0 * ((double)PB.x * XB.x - (double)PB.y * XB.y);
+            }
+        }
+        const double sA = group_sum(aA, red, g);
+        const double sB = two ? group_sum(aB, red, g) : 0.0;
+        if (g.tid == 0) {
+            alpha[J.iA] = (T)sA;
+            if (two) alpha[J.iB] = (T)sB;
         }
     }
 }
@@ -410,6 +518,24 @@ static cudaError_t launch_bwd_t(const RealLaunch& lc, const RealJob* jobs, const
     k<<<lc.count, lc.nthr, smem, st>>>(jobs, lc.first, (const T*)gy, (const T*)h, (const T*)x, (T*)gh, (T*)gx,
                                        (const cx<T>*)tw, (cx<T>*)ws, lc.Lmax, flags, stored);
     return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_multi_t(const RealLaunch& lc, const MultiJob* jobs, const void* h, const void* x, void* y,
+                                  void* alpha, const void* tw, cudaStream_t st) {
+    const size_t smem = real_smem_bytes<T>(lc);
+    auto k = real_multi_kernel<T>;
+    cudaError_t e = ensure_smem(k, smem);
+    if (e != cudaSuccess) return e;
+    k<<<lc.count, lc.nthr, smem, st>>>(jobs, lc.first, (const T*)h, (const T*)x, (T*)y, (T*)alpha,
+                                       (const cx<T>*)tw, lc.Lmax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_real_multi(bool dbl, const RealLaunch& lc, const MultiJob* jobs, const void* h, const void* x,
+                              void* y, void* alpha, const void* tw, cudaStream_t st) {
+    return dbl ? launch_multi_t<double>(lc, jobs, h, x, y, alpha, tw, st)
+               : launch_multi_t<float>(lc, jobs, h, x, y, alpha, tw, st);
 }
 
 cudaError_t launch_real_forward(bool dbl, const RealLaunch& lc, const RealJob* jobs, const void* h, const void* x,

@@ -14,6 +14,8 @@ products and its Section 4 exponential-data-fitting signals):
 * ``batched_square`` -- thousands of square real tensors, order m uniform in
   {3,4,5}, dimension n uniform in [16,1024], h ~ N(0, 1/d_H), x a unit-norm
   Gaussian vector; packed into flat buffers with 16-byte aligned segments.
+* ``batched_distinct`` -- the same batch shape with a different vector in
+  every mode (the y = H x_2 ... x_m and alpha = H x_1 ... x_m products).
 * ``grad_case``      -- m=4, n=4096 batch for the gradient checks.
 * ``edf_1d_signal`` / ``edf_2d_signal`` -- sums of damped complex
   exponentials plus complex Gaussian noise at a given SNR (Sections 4.1, 4.3).
@@ -131,6 +133,37 @@ def batched_square(count=8192, seed=1, orders=(3, 4, 5), n_lo=16, n_hi=1024):
         x = rng.standard_normal(n)
         xs.append(x / np.linalg.norm(x))
     return pack_square(ms, ns, hs, xs)
+
+
+def batched_distinct(count=8192, seed=12, orders=(3, 4, 5), n_lo=16, n_hi=1024):
+    """``count`` square real tensors with a different unit-norm vector in
+    every mode (x_1 .. x_m; x_1 enters only alpha): m ~ U(orders),
+    n ~ U[n_lo, n_hi], h ~ N(0, 1/d).  Returns (Batch, x_offsets) where
+    x_offsets[i] lists the m vector offsets of tensor i in ``Batch.x``."""
+    rng = np.random.default_rng(seed)
+    ms = rng.choice(np.asarray(orders), size=count)
+    ns = rng.integers(n_lo, n_hi + 1, size=count)
+    hs, xs, xoffs = [], [], []
+    xo = 0
+    for m, n in zip(ms, ns):
+        d = generating_length([n] * m)
+        hs.append(rng.standard_normal(d) / np.sqrt(d))
+        offs = []
+        for _ in range(m):
+            x = rng.standard_normal(n)
+            xs.append(x / np.linalg.norm(x))
+            offs.append(xo)
+            xo += _align(n)
+        xoffs.append(offs)
+    b = pack_square(ms, ns, hs, [np.zeros(1)] * count)
+    X = np.zeros(max(xo, 1))
+    k = 0
+    for offs, n in zip(xoffs, ns):
+        for o in offs:
+            X[o: o + n] = xs[k]
+            k += 1
+    b.x = X
+    return b, xoffs
 
 
 def grad_case(batch=64, m=4, n=4096, seed=3, target_scale=0.01):

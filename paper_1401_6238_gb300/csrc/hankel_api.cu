@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -197,10 +198,27 @@ struct hankel_plan_s {
     // streams the independent launches of one call fork onto, and events
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> events;  // [0] fork, [1 + i] join of streams[i]
+    // hankel_txv_host pipeline: sub-plans over contiguous descriptor ranges
+    // whose copies in and out overlap the other ranges' kernels
+    bool from_descs = true;  // false for plans made from level-k descriptors
+    bool chunks_tried = false;
+    struct Chunk {
+        hankel_plan_s* plan;
+        int64_t first;
+        int64_t hlo, hhi, xlo, xhi, ylo, yhi;  // element ranges the chunk reads / writes
+    };
+    std::vector<Chunk> chunks;
+    cudaStream_t s_in = nullptr, s_out = nullptr, s_cap = nullptr;
+    std::vector<cudaEvent_t> pipe_events;  // [0] start, [1] end, then in / done per chunk
+    // the pipeline as a CUDA graph, replayed while the host buffers are the same
+    cudaGraphExec_t graph = nullptr;
+    const void* gkey[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t cap_in = nullptr, cap_out = nullptr;
 };
 
 namespace {
 
+void free_plan(hankel_plan_s* p);
 void free_plan(hankel_plan_s* p) {
     if (!p) return;
     cudaFree(p->d_fwd);
@@ -214,6 +232,14 @@ void free_plan(hankel_plan_s* p) {
     cudaFree(p->s_a);
     for (auto st : p->streams) cudaStreamDestroy(st);
     for (auto ev : p->events) cudaEventDestroy(ev);
+    for (auto& c : p->chunks) free_plan(c.plan);
+    if (p->s_in) cudaStreamDestroy(p->s_in);
+    if (p->s_out) cudaStreamDestroy(p->s_out);
+    if (p->s_cap) cudaStreamDestroy(p->s_cap);
+    if (p->graph) cudaGraphExecDestroy(p->graph);
+    if (p->cap_in) cudaEventDestroy(p->cap_in);
+    if (p->cap_out) cudaEventDestroy(p->cap_out);
+    for (auto ev : p->pipe_events) cudaEventDestroy(ev);
     if (p->gen) hk::general_destroy(p->gen);
     delete p;
 }
@@ -540,6 +566,143 @@ hankel_status build_multi_path(hankel_plan_s* p) {
     return make_streams(p, opl ? 0 : p->multi_launches.size());
 }
 
+// Element ranges of h, x and y that one descriptor reads or writes.
+void desc_ranges(const hankel_desc& d, uint32_t flags, int64_t r[6]) {
+    const bool block = flags & HANKEL_BLOCK, anti = flags & HANKEL_ANTICIRCULANT;
+    int64_t sn = 0, sN = 0;
+    for (int q = 0; q < d.m; ++q) {
+        sn += d.n[q];
+        sN += block ? d.N[q] : 1;
+    }
+    const int64_t N0 = block ? d.N[0] : 1;
+    const int64_t hl = anti ? (int64_t)d.n[0] * N0 : (sn - d.m + 1) * (block ? sN - d.m + 1 : 1);
+    r[0] = d.h_off;
+    r[1] = d.h_off + hl;
+    const int nx = (flags & HANKEL_SAME_X) ? 1 : d.m;
+    r[2] = INT64_MAX;
+    r[3] = 0;
+    for (int q = 0; q < nx; ++q) {
+        r[2] = std::min<int64_t>(r[2], d.x_off[q]);
+        r[3] = std::max<int64_t>(r[3], d.x_off[q] + (int64_t)d.n[q] * (block ? d.N[q] : 1));
+    }
+    r[4] = d.y_off;
+    r[5] = d.y_off + (int64_t)d.n[0] * N0;
+}
+
+// Split a plan's descriptors into contiguous ranges with one sub-plan each
+// (made once, on the first pipelined hankel_txv_host).
+hankel_status build_chunks(hankel_plan_s* p, int nchunks) {
+    const int64_t count = (int64_t)p->descs.size();
+    for (int c = 0; c < nchunks; ++c) {
+        const int64_t c0 = count * c / nchunks, c1 = count * (c + 1) / nchunks;
+        if (c1 <= c0) continue;
+        hankel_plan_s::Chunk ch{nullptr, c0, INT64_MAX, 0, INT64_MAX, 0, INT64_MAX, 0};
+        for (int64_t i = c0; i < c1; ++i) {
+            int64_t r[6];
+            desc_ranges(p->descs[i], p->flags, r);
+            ch.hlo = std::min(ch.hlo, r[0]);
+            ch.hhi = std::max(ch.hhi, r[1]);
+            ch.xlo = std::min(ch.xlo, r[2]);
+            ch.xhi = std::max(ch.xhi, r[3]);
+            ch.ylo = std::min(ch.ylo, r[4]);
+            ch.yhi = std::max(ch.yhi, r[5]);
+        }
+        const hankel_status s = hankel_plan(&ch.plan, p->descs.data() + c0, c1 - c0, p->dtype, p->flags);
+        if (s != HANKEL_OK) return s;
+        p->chunks.push_back(ch);
+    }
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&p->s_in, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(e, "cudaStreamCreate");
+    if ((e = cudaStreamCreateWithFlags(&p->s_out, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(e, "cudaStreamCreate");
+    if ((e = cudaStreamCreateWithFlags(&p->s_cap, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(e, "cudaStreamCreate");
+    if ((e = cudaEventCreateWithFlags(&p->cap_in, cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(e, "cudaEventCreate");
+    if ((e = cudaEventCreateWithFlags(&p->cap_out, cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(e, "cudaEventCreate");
+    for (size_t i = 0; i < 2 + 2 * p->chunks.size(); ++i) {
+        cudaEvent_t ev;
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(e, "cudaEventCreate");
+        p->pipe_events.push_back(ev);
+    }
+    return HANKEL_OK;
+}
+
+// Enqueue the whole pipeline on stream s: copies in on s_in, each range's
+// kernels on s, copies out on s_out, all joined back into s.
+hankel_status enqueue_pipeline(hankel_plan_s* p, const void* h, const void* x, void* y, void* alpha, cudaStream_t s) {
+    const size_t es = elem_size(p->dtype);
+    cudaError_t e;
+    cudaEvent_t ev_start = p->pipe_events[0], ev_end = p->pipe_events[1];
+    if ((e = cudaEventRecord(ev_start, s)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    if ((e = cudaStreamWaitEvent(p->s_in, ev_start, 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+    if ((e = cudaStreamWaitEvent(p->s_out, ev_start, 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+    for (size_t c = 0; c < p->chunks.size(); ++c) {
+        const auto& ch = p->chunks[c];
+        cudaEvent_t ev_in = p->pipe_events[2 + 2 * c], ev_done = p->pipe_events[3 + 2 * c];
+        if ((e = cudaMemcpyAsync((char*)p->s_h + ch.hlo * es, (const char*)h + ch.hlo * es, (ch.hhi - ch.hlo) * es,
+                                 cudaMemcpyHostToDevice, p->s_in)) != cudaSuccess)
+            return cuda_fail(e, "H2D");
+        if ((e = cudaMemcpyAsync((char*)p->s_x + ch.xlo * es, (const char*)x + ch.xlo * es, (ch.xhi - ch.xlo) * es,
+                                 cudaMemcpyHostToDevice, p->s_in)) != cudaSuccess)
+            return cuda_fail(e, "H2D");
+        if ((e = cudaEventRecord(ev_in, p->s_in)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+        if ((e = cudaStreamWaitEvent(s, ev_in, 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+        void* ya = y ? p->s_y : nullptr;
+        void* aa = alpha ? (void*)((char*)p->s_a + ch.first * es) : nullptr;
+        const hankel_stream_t hs = (hankel_stream_t)s;
+        const hankel_status st = (p->flags & HANKEL_BLOCK) ? hankel_txv_block(ch.plan, p->s_h, p->s_x, ya, aa, hs)
+                                                           : hankel_txv(ch.plan, p->s_h, p->s_x, ya, aa, hs);
+        if (st != HANKEL_OK) return st;
+        if ((e = cudaEventRecord(ev_done, s)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+        if (y) {
+            // ranges copied out later repeat any value copied earlier, so the
+            // last copy of every output is the computed one
+            if ((e = cudaStreamWaitEvent(p->s_out, ev_done, 0)) != cudaSuccess)
+                return cuda_fail(e, "cudaStreamWaitEvent");
+            if ((e = cudaMemcpyAsync((char*)y + ch.ylo * es, (const char*)p->s_y + ch.ylo * es, (ch.yhi - ch.ylo) * es,
+                                     cudaMemcpyDeviceToHost, p->s_out)) != cudaSuccess)
+                return cuda_fail(e, "D2H");
+        }
+    }
+    if (alpha && (e = cudaMemcpyAsync(alpha, p->s_a, p->descs.size() * es, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_fail(e, "D2H");
+    if ((e = cudaEventRecord(ev_end, p->s_out)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    if ((e = cudaStreamWaitEvent(s, ev_end, 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+    return HANKEL_OK;
+}
+
+// Record the pipeline for these host buffers as a CUDA graph (after an eager
+// run has finished, so every kernel attribute is already set).  On any
+// failure the plan keeps running the pipeline eagerly.
+void capture_pipeline(hankel_plan_s* p, const void* h, const void* x, void* y, void* alpha) {
+    if (p->graph) {
+        cudaGraphExecDestroy(p->graph);
+        p->graph = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(p->s_cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    const hankel_status s = enqueue_pipeline(p, h, x, y, alpha, p->s_cap);
+    const cudaError_t e = cudaStreamEndCapture(p->s_cap, &graph);
+    if (s == HANKEL_OK && e == cudaSuccess && graph != nullptr &&
+        cudaGraphInstantiate(&p->graph, graph, 0) == cudaSuccess) {
+        p->gkey[0] = h;
+        p->gkey[1] = x;
+        p->gkey[2] = y;
+        p->gkey[3] = alpha;
+    } else {
+        p->graph = nullptr;
+        cudaGetLastError();
+    }
+    if (graph) cudaGraphDestroy(graph);
+}
+
 // The general-path program of a plan (made on first use for plans whose
 // forward products run on a fused path but whose adjoint runs here).
 hankel_status ensure_general(hankel_plan_s* p) {
@@ -672,6 +835,7 @@ hankel_status hankel_plan_multilevel(hankel_plan_t* out, const hankel_mdesc* des
     if (!p) return fail(HANKEL_ENOMEM, "host allocation failed");
     p->dtype = dtype;
     p->flags = flags | HANKEL_BLOCK;  // computes through hankel_txv_block
+    p->from_descs = false;
     cudaGetDevice(&p->device);
     std::vector<hankel_mdesc> md(descs, descs + count);
     p->descs.resize(count);  // only the count is read back (hankel_plan_query, staging sizes)
@@ -717,6 +881,39 @@ hankel_status hankel_txv_host(hankel_plan_t p, const void* h, const void* x, voi
         if ((e = cudaMalloc(&p->s_a, ab)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(staging)");
     }
     cudaStream_t st = (cudaStream_t)stream;
+    // Large batches run as a pipeline of contiguous descriptor ranges: the
+    // copies in of range c + 1 and the copy out of range c - 1 overlap the
+    // kernels of range c.
+    constexpr int kChunks = 4;
+    const bool pipe = p->from_descs && (int64_t)p->descs.size() >= 32 * kChunks && hb + xb >= (8u << 20);
+    if (pipe && !p->chunks_tried) {
+        p->chunks_tried = true;
+        if (build_chunks(p, kChunks) != HANKEL_OK) {
+            for (auto& c : p->chunks) free_plan(c.plan);
+            p->chunks.clear();
+        }
+    }
+    if (pipe && !p->chunks.empty()) {
+        // the pipeline runs on the plan's own stream s_cap, ordered after the
+        // caller's stream and joined back into it; with the same host buffers
+        // as the previous call it is one CUDA graph launch (the host cost of
+        // the ~200 calls that enqueue it would otherwise pace the copies)
+        const void* key[4] = {h, x, y, alpha};
+        const bool replay = p->graph && std::equal(key, key + 4, p->gkey);
+        if ((e = cudaEventRecord(p->cap_in, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+        if ((e = cudaStreamWaitEvent(p->s_cap, p->cap_in, 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+        if (replay) {
+            if ((e = cudaGraphLaunch(p->graph, p->s_cap)) != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+        } else {
+            const hankel_status s = enqueue_pipeline(p, h, x, y, alpha, p->s_cap);
+            if (s != HANKEL_OK) return s;
+        }
+        if ((e = cudaEventRecord(p->cap_out, p->s_cap)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+        if ((e = cudaStreamWaitEvent(st, p->cap_out, 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "stream synchronize");
+        if (!replay) capture_pipeline(p, h, x, y, alpha);
+        return HANKEL_OK;
+    }
     if ((e = cudaMemcpyAsync(p->s_h, h, hb, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_fail(e, "H2D");
     if ((e = cudaMemcpyAsync(p->s_x, x, xb, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_fail(e, "H2D");
     hankel_status s = (p->flags & HANKEL_BLOCK)

@@ -153,10 +153,12 @@ def profiled_traffic():
     import hashlib
     path = os.path.join(ROOT, "profiles", "real_fwd_traffic.json")
     try:
-        rec = json.load(open(path))
+        with open(path) as fh:
+            rec = json.load(fh)
         h = hashlib.sha256()
         for f in rec["sources"]:
-            h.update(open(os.path.join(ROOT, f), "rb").read())
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                h.update(fh.read())
         return rec["bytes_per_step"] if h.hexdigest() == rec["sources_sha256"] else None
     except Exception:
         return None

@@ -21,7 +21,8 @@ def lib():
 
 
 def declared_functions():
-    src = open(os.path.join(ROOT, "include", "hankel.h")).read()
+    with open(os.path.join(ROOT, "include", "hankel.h")) as f:
+        src = f.read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(hankel_[a-z_0-9]+)\s*\(", src)))
 

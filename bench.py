@@ -178,17 +178,16 @@ def timed(fn, steps, warmup, stream):
     return a.elapsed_time(b) / steps
 
 
-def secondary_workloads(dev, stream, steps=10, warmup=3):
-    """The other workloads of the path, timed on the device (inputs resident;
-    these batches are L2-sized, so they measure the kernels, not HBM)."""
+def sec_grad(dev, stream, steps, warmup):
     import torch
     from paper_1401_6238_gb300 import hankel as hk
     from paper_1401_6238_gb300 import workloads as wl
+    f32 = lambda a: torch.tensor(a, dtype=torch.float32, device=dev)
+    c64 = lambda a: torch.tensor(a, dtype=torch.complex64, device=dev)
     out = {}
     # gradient workload: loss through y = H x^{m-1}, m = 4, n = 4096, batch 64
     b = wl.grad_case(batch=64, m=4, n=4096, seed=3)
     plan = hk.Plan(hk.batch_descs(b), hk.R32, hk.SAME_X | hk.STORE_SPECTRA)
-    f32 = lambda a: torch.tensor(a, dtype=torch.float32, device=dev)
     H, X = f32(b.h), f32(b.x)
     Y = torch.zeros(plan.info["y_elems"], dtype=torch.float32, device=dev)
     G = f32(np.random.default_rng(0).standard_normal(plan.info["y_elems"]))
@@ -202,6 +201,16 @@ def secondary_workloads(dev, stream, steps=10, warmup=3):
     out["grad"] = {"workload": "m=4, n=4096 (d=16381, L=16384), batch 64, FP32 forward + backward (spectra kept)",
                    "value": 64 / (ms / 1e3), "unit": "forward+backward products/s", "ms_per_step": ms}
     plan.close()
+    return out
+
+
+def sec_hooi_products(dev, stream, steps, warmup):
+    import torch
+    from paper_1401_6238_gb300 import hankel as hk
+    from paper_1401_6238_gb300 import workloads as wl
+    f32 = lambda a: torch.tensor(a, dtype=torch.float32, device=dev)
+    c64 = lambda a: torch.tensor(a, dtype=torch.complex64, device=dev)
+    out = {}
     # HOOI tensor-matrix products: 16 x 16 column pairs, shared h, complex64
     R, N = 16, 4094
     s = wl.edf_1d_signal(N=N, seed=4)
@@ -217,7 +226,6 @@ def secondary_workloads(dev, stream, steps=10, warmup=3):
         descs[k]["x_off"][2] = R * dims[1] + j * dims[2]
         descs[k]["y_off"] = k * dims[0]
     plan = hk.Plan(descs, hk.C64, 0)
-    c64 = lambda a: torch.tensor(a, dtype=torch.complex64, device=dev)
     Hs, Xs = c64(s), c64(np.concatenate([U.T.reshape(-1), V.T.reshape(-1)]))
     Ys = torch.zeros(R * R * dims[0], dtype=torch.complex64, device=dev)
     ms = timed(lambda: plan.txv(Hs, Xs, Ys, None, stream), steps, warmup, stream)
@@ -225,6 +233,16 @@ def secondary_workloads(dev, stream, steps=10, warmup=3):
                                         "(1366 x 1365 x 1365), 16 x 16 column pairs H x2 u_i x3 v_j",
                             "value": R * R / (ms / 1e3), "unit": "products/s", "ms_per_step": ms}
     plan.close()
+    return out
+
+
+def sec_bhhb(dev, stream, steps, warmup):
+    import torch
+    from paper_1401_6238_gb300 import hankel as hk
+    from paper_1401_6238_gb300 import workloads as wl
+    f32 = lambda a: torch.tensor(a, dtype=torch.float32, device=dev)
+    c64 = lambda a: torch.tensor(a, dtype=torch.complex64, device=dev)
+    out = {}
     # 2D block (BHHB) products: 256 x 256 signal, blocks 86^3 x 86^3, 32 triples
     count = 32
     S = wl.edf_2d_signal(seed=5)
@@ -250,6 +268,16 @@ def secondary_workloads(dev, stream, steps=10, warmup=3):
                    "value": count / ((ms_f + ms_b) / 1e3), "unit": "forward+adjoint products/s",
                    "forward_ms": ms_f, "adjoint_ms": ms_b}
     plan.close()
+    return out
+
+
+def sec_distinct(dev, stream, steps, warmup):
+    import torch
+    from paper_1401_6238_gb300 import hankel as hk
+    from paper_1401_6238_gb300 import workloads as wl
+    f32 = lambda a: torch.tensor(a, dtype=torch.float32, device=dev)
+    c64 = lambda a: torch.tensor(a, dtype=torch.complex64, device=dev)
+    out = {}
     # distinct vectors per mode (Section 3's m + 1 transform form): the
     # 8192-tensor batch shape with x_1 .. x_m per tensor, FP32
     bd, xoffs = wl.batched_distinct(8192, seed=12)
@@ -272,6 +300,16 @@ def secondary_workloads(dev, stream, steps=10, warmup=3):
                        "value": len(bd) / (ms_y / 1e3), "unit": "products/s", "y_ms": ms_y, "y_and_alpha_ms": ms_ya,
                        "jobs": plan.info["jobs"], "launches": plan.info["launches"]}
     plan.close()
+    return out
+
+
+def sec_level3(dev, stream, steps, warmup):
+    import torch
+    from paper_1401_6238_gb300 import hankel as hk
+    from paper_1401_6238_gb300 import workloads as wl
+    f32 = lambda a: torch.tensor(a, dtype=torch.float32, device=dev)
+    c64 = lambda a: torch.tensor(a, dtype=torch.complex64, device=dev)
+    out = {}
     # level-3 block Hankel products (Section 2.2): a 64^3 3D signal as
     # generating tensor, sizes (22,22,22) at every level, 32 vector triples
     count, n3 = 32, 22 ** 3
@@ -293,7 +331,23 @@ def secondary_workloads(dev, stream, steps=10, warmup=3):
                      "forward_ms": ms_f, "adjoint_ms": ms_b, "launches": plan.info["launches"],
                      "workspace_bytes": plan.info["workspace_bytes"]}
     plan.close()
-    out.update(edf_workloads(dev, stream))
+    return out
+
+
+SECONDARY = {"grad": sec_grad, "hooi_products": sec_hooi_products, "bhhb": sec_bhhb, "distinct": sec_distinct,
+             "level3": sec_level3}
+
+
+def secondary_workloads(dev, stream, steps=10, warmup=3, only=None):
+    """The other workloads of the path, timed on the device (inputs resident;
+    these batches are L2-sized, so they measure the kernels, not HBM);
+    ``only`` names a subset (SECONDARY keys and "edf")."""
+    out = {}
+    for name, fn in SECONDARY.items():
+        if only is None or name in only:
+            out.update(fn(dev, stream, steps, warmup))
+    if only is None or "edf" in only:
+        out.update(edf_workloads(dev, stream))
     return out
 
 
@@ -377,9 +431,19 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-secondary", action="store_true", help="skip the secondary workloads")
+    ap.add_argument("--secondary", default=None,
+                    help="comma-separated secondary workloads to run alone (grad, hooi_products, bhhb, distinct, "
+                         "level3, edf); prints their JSON and exits")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.secondary:
+        import torch
+        torch.cuda.set_device(0)
+        only = [w.strip() for w in args.secondary.split(",") if w.strip()]
+        res = secondary_workloads(torch.device("cuda", 0), torch.cuda.current_stream(), args.steps, args.warmup, only)
+        print(json.dumps({"secondary": res}))
+        return
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

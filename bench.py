@@ -164,6 +164,19 @@ def profiled_traffic():
         return None
 
 
+FP32_LANES_PER_SM, SMS = 128, 152
+
+
+def alu_roofline(flops, kernel_ms, clocks):
+    """FP32 CUDA-core roofline of the forward step (flops per step / kernel
+    time against 2 x lanes x SMs x the median sampled SM clock)."""
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    peak = 2.0 * FP32_LANES_PER_SM * SMS * mhz * 1e6 / 1e12
+    achieved = flops / (kernel_ms / 1000.0) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "flops_per_step": flops, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % mhz}
+
+
 def timed(fn, steps, warmup, stream):
     import torch
     for _ in range(warmup):
@@ -514,6 +527,12 @@ def main():
     kernel_ms = float(np.mean(step_ms))
     achieved = alg_bytes / (kernel_ms / 1000.0) / 1e9
     traffic = profiled_traffic()
+    # the same step against the FP32 CUDA-core roofline: 5 L log2 L flops per
+    # complex length-L transform, three transforms per pair of tensors (1.5
+    # per tensor); the spectrum products are not counted.  Peak: 152 SMs x
+    # 128 FP32 lanes x 2 flops (FMA) x the SM clock sampled during the run.
+    lens = [hk.hankel_fft_length(int(m * (n - 1) + 1)) for m, n in zip(batch.orders, batch.dims)]
+    alg_flops = float(sum(1.5 * 5.0 * L * np.log2(L) for L in lens))
 
     # the same step replayed from a CUDA graph (the launches and the plan's
     # stream fork/join captured once)
@@ -610,6 +629,7 @@ def main():
                              "frac": achieved / peak, "traffic": traffic,
                              "peak_source": peak_src, "kernel": "real_fwd_kernel<float>",
                              "algorithmic_bytes_per_step": alg_bytes},
+                "roofline_alu": alu_roofline(alg_flops, kernel_ms, clocks),
                 "e2e": e2e, "gpu_launches": int(info["launches"]) * args.steps,
                 "plan": info, "fp64_plain": fp64, "cpu_baseline": cpu, "clocks": clocks,
                 "secondary": secondary, "graph_replay": graph,

@@ -327,8 +327,11 @@ int max_len_for(int buffers, size_t csize) {
 void make_launches(std::vector<hk::RealJob>& jobs, std::vector<hk::RealLaunch>& launches, bool one_per_launch,
                    int single_buffers, int max_single_L) {
     // kind: 0 pair (three shared buffers), 1 single (two), 2 single with
-    // global scratch (shared memory holds only twiddles)
-    auto kind = [&](const hk::RealJob& j) { return !j.single ? 0 : (j.P.L > max_single_L ? 2 : 1); };
+    // global scratch (shared memory holds only twiddles), 3 split single
+    // (two blocks of two buffers of L/2)
+    auto kind = [&](const hk::RealJob& j) {
+        return !j.single ? 0 : (j.split ? 3 : (j.P.L > max_single_L ? 2 : 1));
+    };
     std::stable_sort(jobs.begin(), jobs.end(), [&](const hk::RealJob& a, const hk::RealJob& b) {
         if (kind(a) != kind(b)) return kind(a) < kind(b);
         return a.P.L > b.P.L;
@@ -339,9 +342,9 @@ void make_launches(std::vector<hk::RealJob>& jobs, std::vector<hk::RealLaunch>& 
         hk::RealLaunch lc;
         lc.first = (int)i;
         lc.nthr = nthr_of(L0);
-        lc.emax = 0;
         lc.Lmax = L0;
-        lc.arrays = kind(jobs[i]) == 0 ? 3 : (kind(jobs[i]) == 1 ? single_buffers : 0);
+        lc.arrays = kind(jobs[i]) == 0 ? 3 : (kind(jobs[i]) == 1 ? single_buffers : (kind(jobs[i]) == 3 ? 2 : 0));
+        lc.split = kind(jobs[i]) == 3 ? 1 : 0;
         size_t j = i + 1;
         if (!one_per_launch)
             while (j < jobs.size() && nthr_of(jobs[j].P.L) == lc.nthr && kind(jobs[j]) == kind(jobs[i])) ++j;
@@ -381,6 +384,14 @@ hankel_status make_streams(hankel_plan_s* p, size_t nlaunch) {
         p->events.push_back(ev);
     }
     return HANKEL_OK;
+}
+
+// L / 2 when a single job of length L can run split (L even, L / 2 one of
+// the planner's lengths that fits two shared buffers), else 0.
+int split_length(const hankel_plan_s* p, int L) {
+    const int max_single_L = max_len_for(2, 2 * real_size(p->dtype));
+    if (L % 2 != 0 || L / 2 > max_single_L || lengths().find(L / 2) == nullptr) return 0;
+    return L / 2;
 }
 
 hankel_status build_real_path(hankel_plan_s* p) {
@@ -452,6 +463,17 @@ hankel_status build_real_path(hankel_plan_s* p) {
         J.iB = -1;
         p->bwd_jobs.push_back(J);
     }
+    // single jobs too long for one block's shared memory run as split jobs
+    // (two blocks of length L/2) where L/2 is a transform length of the plan
+    for (auto* v : {&p->fwd_jobs, &p->bwd_jobs})
+        for (auto& J : *v) {
+            const int L = J.P.L;
+            if (J.single && L > max_single_L && split_length(p, L) > 0) {
+                J.split = 1;
+                J.twL = p->tw_off.at(L);
+                J.P = fft_plan_of(p, L / 2);
+            }
+        }
     const bool opl = (p->flags & HANKEL_ONE_PER_LAUNCH) != 0;
     make_launches(p->fwd_jobs, p->fwd_launches, opl, 2, max_single_L);
     make_launches(p->bwd_jobs, p->bwd_launches, opl, 2, max_single_L);
@@ -545,7 +567,7 @@ hankel_status build_multi_path(hankel_plan_s* p) {
         hk::RealLaunch lc;
         lc.first = (int)i;
         lc.nthr = nthr_of(p->multi_jobs[i].P.L);
-        lc.emax = 0;
+        lc.split = 0;
         lc.Lmax = p->multi_jobs[i].P.L;
         lc.arrays = 3;
         size_t j = i + 1;
@@ -789,6 +811,11 @@ hankel_status hankel_plan(hankel_plan_t* out, const hankel_desc* descs, int64_t 
         s = upload_twiddles(p, Ls);
         if (s == HANKEL_OK) s = build_multi_path(p);
     } else if (p->real_path) {
+        // split jobs also need the tables of half their length
+        const int max_single_L = max_len_for(2, 2 * real_size(dtype));
+        const size_t nL = Ls.size();
+        for (size_t i = 0; i < nL; ++i)
+            if (Ls[i] > max_single_L && split_length(p, Ls[i]) > 0) Ls.push_back(Ls[i] / 2);
         s = upload_twiddles(p, Ls);
         if (s == HANKEL_OK) s = build_real_path(p);
     } else {

@@ -21,6 +21,10 @@
 // reversed) and grad_x (imaginary part).
 #include <cuda_runtime.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "fft_stage.cuh"
 #include "launch.h"
 
@@ -438,6 +442,196 @@ __global__ void __launch_bounds__(512) real_bwd_global_kernel(const RealJob* __r
     fft_global<T>(P, GLd<T>{nullptr, 0, nullptr, 0}, F, G, F, store, false, tw, g);
 }
 
+// ---------------------------------------------------------------- split jobs
+// A length L = 2M transform as two length-M transforms (decimation in
+// frequency): with u the input, X[2k + c] = sum_n v_c[n] w_M^{nk} where
+// v_0[n] = u[n] + u[n + M] and v_1[n] = (u[n] - u[n + M]) w_L^n.  Block c of a
+// job stages v_c in shared memory, transforms it and stores the bins 2k + c,
+// so a job's two blocks run on two SMs and every pass stays in shared memory.
+
+// Real signals a + i b, zero-padded (the same reading as GLd).
+template <typename T>
+struct PairSrc {
+    const T* a;
+    int na;
+    const T* b;
+    int nb;
+    __device__ __forceinline__ cx<T> operator()(int i) const {
+        return mk<T>(i < na ? a[i] : T(0), i < nb ? b[i] : T(0));
+    }
+};
+
+// Forward spectral product P_k = ifft(h~)_k X_k^{m-1} from the stored
+// spectrum S = fft(h~ + i x~).
+template <typename T>
+struct ProductSrc {
+    const cx<T>* S;
+    int L, m;
+    T invL;
+    bool fp64;
+    __device__ __forceinline__ cx<T> operator()(int k) const {
+        const int kc = (k == 0) ? 0 : L - k;
+        cx<T> Hk, Xk;
+        unpack(S[k], conjg(S[kc]), Hk, Xk);
+        double at;
+        return fp64 ? product<double>(Hk, Xk, m, invL, at, false) : product<T>(Hk, Xk, m, invL, at, false);
+    }
+};
+
+// Adjoint spectrum Q_k from U = fft(h~ + i x~) and G = fft(g~).
+template <typename T>
+struct AdjointSrc {
+    const cx<T>* U;
+    const cx<T>* G;
+    int L, m;
+    T invL;
+    bool fp64;
+    __device__ __forceinline__ cx<T> operator()(int k) const {
+        const int kc = (k == 0) ? 0 : L - k;
+        return fp64 ? adjoint_bin<double>(U[k], conjg(U[kc]), G[k], m, invL)
+                    : adjoint_bin<T>(U[k], conjg(U[kc]), G[k], m, invL);
+    }
+};
+
+// v_c[n] into shared memory (padded layout), n < M.
+template <typename T, class Src>
+__device__ __forceinline__ void dif_stage(cx<T>* buf, const Src& u, int M, int c, const TwTab<T>& twL,
+                                          const Group& g) {
+    for (int n = g.tid; n < M; n += g.nthr) {
+        const cx<T> a = u(n), b = u(n + M);
+        buf[sp(n)] = (c == 0) ? a + b : cmul(a - b, twL(n));
+    }
+}
+
+template <typename T>
+struct SplitSt {  // complex bins 2k + c of a length-2M spectrum
+    cx<T>* p;
+    int c;
+    __device__ __forceinline__ void operator()(int k, cx<T> v) const { p[2 * k + c] = v; }
+};
+
+template <typename T>
+struct SplitRealSt {  // real part of the bins 2k + c, truncated to n
+    T* y;
+    int n, c;
+    __device__ __forceinline__ void operator()(int k, cx<T> v) const {
+        const int i = 2 * k + c;
+        if (i < n) y[i] = v.x;
+    }
+};
+
+template <typename T>
+struct SplitAdjSt {  // AdjSt at the bins 2k + c
+    AdjSt<T> st;
+    int c;
+    __device__ __forceinline__ void operator()(int k, cx<T> v) const { st(2 * k + c, v); }
+};
+
+// Shared-memory layout of the split kernels: twiddle tables of lengths M and
+// L = 2M, then two padded buffers of Mmax.
+template <typename T>
+struct SplitSmem {
+    TwTab<T> twM, twL;
+    cx<T>*b0, *b1;
+};
+
+template <typename T>
+__device__ __forceinline__ SplitSmem<T> split_smem(unsigned char* raw, const RealJob& J, const cx<T>* tw_all,
+                                                  int Mmax, const Group& g) {
+    cx<T>* t0 = reinterpret_cast<cx<T>*>(raw + RED_BYTES);
+    cx<T>* t1 = t0 + TW_SMEM;
+    SplitSmem<T> s;
+    s.twM = load_twiddles(t0, tw_all + J.P.tw_off, J.P.L, g);
+    s.twL = load_twiddles(t1, tw_all + J.twL, 2 * J.P.L, g);
+    s.b0 = t1 + TW_SMEM;
+    s.b1 = s.b0 + smem_elems(Mmax);
+    return s;
+}
+
+// Spectra of split jobs: block (job, source, c); sources (bit mask `srcs`):
+// bit 0 the packed input h~ + i x~ into the tensor's spectrum slot wsA,
+// bit 1 the upstream gradient g~ into the job's scratch wsB.
+template <typename T>
+__global__ void __launch_bounds__(512) split_spectrum_kernel(const RealJob* __restrict__ jobs, int first,
+                                                              const T* __restrict__ h, const T* __restrict__ x,
+                                                              const T* __restrict__ gy, int srcs, cx<T>* ws,
+                                                              const cx<T>* __restrict__ tw_all, int Mmax) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nsrc = (srcs & 1) + ((srcs >> 1) & 1);
+    const int c = blockIdx.x & 1;
+    const int s_i = (blockIdx.x >> 1) % nsrc;
+    const int src = (nsrc == 2) ? s_i : ((srcs & 1) ? 0 : 1);
+    const RealJob J = jobs[first + (int)(blockIdx.x >> 1) / nsrc];
+    const Group g{(int)threadIdx.x, (int)blockDim.x, 0};
+    const SplitSmem<T> sm = split_smem(smem_raw, J, tw_all, Mmax, g);
+    const int M = J.P.L;
+    g.sync();
+    if (src == 0)
+        dif_stage(sm.b0, PairSrc<T>{h + J.hA, J.dA, x + J.xA, J.nA}, M, c, sm.twL, g);
+    else
+        dif_stage(sm.b0, PairSrc<T>{gy + J.yA, J.nA, nullptr, 0}, M, c, sm.twL, g);
+    g.sync();
+    cx<T>* dst = ws + (src == 0 ? J.wsA : J.wsB);
+    fft_stage<T>(J.P, GLd<T>{nullptr, 0, nullptr, 0}, sm.b0, sm.b1, sm.b0, SplitSt<T>{dst, c}, false, sm.twM, g);
+}
+
+// y = fft(P)[0:n] and alpha for split jobs, from the spectra in wsA.
+template <typename T>
+__global__ void __launch_bounds__(512) split_forward_kernel(const RealJob* __restrict__ jobs, int first,
+                                                             T* __restrict__ y, T* __restrict__ alpha,
+                                                             const cx<T>* ws, const cx<T>* __restrict__ tw_all,
+                                                             int Mmax, int flags) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* red = reinterpret_cast<double*>(smem_raw);
+    const int c = blockIdx.x & 1;
+    const RealJob J = jobs[first + (int)(blockIdx.x >> 1)];
+    const Group g{(int)threadIdx.x, (int)blockDim.x, 0};
+    const SplitSmem<T> sm = split_smem(smem_raw, J, tw_all, Mmax, g);
+    const int M = J.P.L, L = 2 * M;
+    const bool fp64 = (flags & HANKEL_FP64_POWER) != 0;
+    const T invL = T(1) / T(L);
+    const cx<T>* S = ws + J.wsA;
+    g.sync();
+    if (y != nullptr) {
+        dif_stage(sm.b0, ProductSrc<T>{S, L, J.mA, invL, fp64}, M, c, sm.twL, g);
+        g.sync();
+        fft_stage<T>(J.P, GLd<T>{nullptr, 0, nullptr, 0}, sm.b0, sm.b1, sm.b0, SplitRealSt<T>{y + J.yA, J.nA, c},
+                     false, sm.twM, g);
+    }
+    if (alpha != nullptr && c == 0) {
+        double aA = 0.0;
+        for (int k = g.tid; k <= L / 2; k += g.nthr) {
+            const int kc = (k == 0) ? 0 : L - k;
+            cx<T> Hk, Xk;
+            unpack(S[k], conjg(S[kc]), Hk, Xk);
+            aA += alpha_term(Hk, Xk, J.mA, invL, fp64, k, kc);
+        }
+        const double sA = group_sum(aA, red, g);
+        if (g.tid == 0) alpha[J.iA] = (T)sA;
+    }
+}
+
+// Gradients of split jobs from U (wsA) and G (wsB).
+template <typename T>
+__global__ void __launch_bounds__(512) split_backward_kernel(const RealJob* __restrict__ jobs, int first,
+                                                              T* __restrict__ gh, T* __restrict__ gx, const cx<T>* ws,
+                                                              const cx<T>* __restrict__ tw_all, int Mmax,
+                                                              int flags) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int c = blockIdx.x & 1;
+    const RealJob J = jobs[first + (int)(blockIdx.x >> 1)];
+    const Group g{(int)threadIdx.x, (int)blockDim.x, 0};
+    const SplitSmem<T> sm = split_smem(smem_raw, J, tw_all, Mmax, g);
+    const int M = J.P.L, L = 2 * M;
+    const bool fp64 = (flags & HANKEL_FP64_POWER) != 0;
+    const T invL = T(1) / T(L);
+    g.sync();
+    dif_stage(sm.b0, AdjointSrc<T>{ws + J.wsA, ws + J.wsB, L, J.mA, invL, fp64}, M, c, sm.twL, g);
+    g.sync();
+    const AdjSt<T> st{gh ? gh + J.hA : nullptr, J.dA, gx ? gx + J.xA : nullptr, J.nA, L};
+    fft_stage<T>(J.P, GLd<T>{nullptr, 0, nullptr, 0}, sm.b0, sm.b1, sm.b0, SplitAdjSt<T>{st, c}, false, sm.twM, g);
+}
+
 // Two-level twiddle table of length L (fft_stage.cuh): A[j] = w_L^{64 j},
 // B[j] = w_L^j, from FP64 sincospi rounded to T.
 template <typename T>
@@ -465,18 +659,25 @@ __global__ void twiddle_kernel(cx<T>* out, int L) {
 
 // Raise a kernel's dynamic shared-memory limit only when a launch needs more
 // than already granted (no attribute calls in steady state, so launches can
-// be captured into CUDA graphs).
-template <class K>
-static cudaError_t ensure_smem(K kernel, size_t bytes) {
-    static size_t granted[64] = {0};  // per device, one table per kernel signature
+// be captured into CUDA graphs).  Grants are kept per device and per kernel
+// (kernels of one signature are distinct entries).
+static cudaError_t ensure_smem_fn(const void* fn, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> granted;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    size_t& g = granted[dev & 63];
+    std::lock_guard<std::mutex> lk(mu);
+    size_t& g = granted[std::make_pair(dev, fn)];
     if (bytes <= g) return cudaSuccess;
-    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e == cudaSuccess) g = bytes;
     return e;
+}
+
+template <class K>
+static cudaError_t ensure_smem(K kernel, size_t bytes) {
+    return ensure_smem_fn(reinterpret_cast<const void*>(kernel), bytes);
 }
 
 template <typename T>
@@ -485,8 +686,36 @@ static size_t real_smem_bytes(const RealLaunch& lc) {
 }
 
 template <typename T>
+static size_t split_smem_bytes(const RealLaunch& lc) {
+    return RED_BYTES + ((size_t)2 * TW_SMEM + (size_t)2 * smem_elems(lc.Lmax)) * sizeof(cx<T>);
+}
+
+template <typename T>
+static cudaError_t launch_split_spectra(const RealLaunch& lc, const RealJob* jobs, const void* h, const void* x,
+                                        const void* gy, int srcs, const void* tw, void* ws, cudaStream_t st) {
+    const size_t smem = split_smem_bytes<T>(lc);
+    auto k = split_spectrum_kernel<T>;
+    cudaError_t e = ensure_smem(k, smem);
+    if (e != cudaSuccess) return e;
+    const int nsrc = (srcs & 1) + ((srcs >> 1) & 1);
+    k<<<lc.count * 2 * nsrc, lc.nthr, smem, st>>>(jobs, lc.first, (const T*)h, (const T*)x, (const T*)gy, srcs,
+                                                   (cx<T>*)ws, (const cx<T>*)tw, lc.Lmax);
+    return cudaGetLastError();
+}
+
+template <typename T>
 static cudaError_t launch_fwd_t(const RealLaunch& lc, const RealJob* jobs, const void* h, const void* x, void* y,
                                 void* alpha, const void* tw, void* ws, int flags, cudaStream_t st) {
+    if (lc.split) {
+        cudaError_t e = launch_split_spectra<T>(lc, jobs, h, x, nullptr, 1, tw, ws, st);
+        if (e != cudaSuccess) return e;
+        const size_t smem = split_smem_bytes<T>(lc);
+        auto k = split_forward_kernel<T>;
+        if ((e = ensure_smem(k, smem)) != cudaSuccess) return e;
+        k<<<lc.count * 2, lc.nthr, smem, st>>>(jobs, lc.first, (T*)y, (T*)alpha, (const cx<T>*)ws,
+                                                (const cx<T>*)tw, lc.Lmax, flags);
+        return cudaGetLastError();
+    }
     const size_t smem = real_smem_bytes<T>(lc);
     if (lc.arrays == 0) {
         real_fwd_global_kernel<T><<<lc.count, lc.nthr, smem, st>>>(jobs, lc.first, (const T*)h, (const T*)x, (T*)y,
@@ -505,6 +734,16 @@ template <typename T>
 static cudaError_t launch_bwd_t(const RealLaunch& lc, const RealJob* jobs, const void* gy, const void* h,
                                 const void* x, void* gh, void* gx, const void* tw, void* ws, int flags, int stored,
                                 cudaStream_t st) {
+    if (lc.split) {
+        cudaError_t e = launch_split_spectra<T>(lc, jobs, h, x, gy, stored ? 2 : 3, tw, ws, st);
+        if (e != cudaSuccess) return e;
+        const size_t smem = split_smem_bytes<T>(lc);
+        auto k = split_backward_kernel<T>;
+        if ((e = ensure_smem(k, smem)) != cudaSuccess) return e;
+        k<<<lc.count * 2, lc.nthr, smem, st>>>(jobs, lc.first, (T*)gh, (T*)gx, (const cx<T>*)ws, (const cx<T>*)tw,
+                                                lc.Lmax, flags);
+        return cudaGetLastError();
+    }
     const size_t smem = real_smem_bytes<T>(lc);
     if (lc.arrays == 0) {
         real_bwd_global_kernel<T><<<lc.count, lc.nthr, smem, st>>>(jobs, lc.first, (const T*)gy, (const T*)h,
@@ -573,6 +812,7 @@ cudaError_t launch_stage_twiddles(bool dbl, void* out, const FftPlan& P, cudaStr
 int stage_twiddle_count(const FftPlan& P) { return tw_table_elems(P.L); }
 
 size_t real_launch_smem(bool dbl, const RealLaunch& lc) {
+    if (lc.split) return dbl ? split_smem_bytes<double>(lc) : split_smem_bytes<float>(lc);
     return dbl ? real_smem_bytes<double>(lc) : real_smem_bytes<float>(lc);
 }
 

@@ -47,6 +47,10 @@ def test_full_batch_host_matches_device(dev):
     yh2 = torch.zeros_like(yh)
     plan.txv_host(hh, xh, yh2, None)
     assert torch.equal(yh2, yh)
+    # alpha alone
+    ah2 = torch.zeros_like(ah)
+    plan.txv_host(hh, xh, None, ah2)
+    assert torch.equal(ah2, ah)
     for scale in (2.0, 0.5):
         hh.mul_(scale)
         yh.zero_()

@@ -329,15 +329,19 @@ def _autograd():
     class HankelTxV(torch.autograd.Function):
         """y = H x^{m-1} per descriptor, differentiable in h and x.
 
-        forward(h, x, plan) -> y (flat buffer of plan.info['y_elems']).  The
-        backward runs the library's adjoint kernels; with a plan made with
-        STORE_SPECTRA it reuses the spectra of the forward call.
+        forward(h, x, plan) -> y (flat buffer of plan.info['y_elems']); block
+        and level-k plans run through txv_block.  The backward runs the
+        library's adjoint kernels; with a plan made with STORE_SPECTRA it
+        reuses the spectra of the forward call.
         """
 
         @staticmethod
         def forward(ctx, h, x, plan):
             y = torch.zeros(plan.info["y_elems"], dtype=h.dtype, device=h.device)
-            plan.txv(h.contiguous(), x.contiguous(), y)
+            if plan.flags & BLOCK:  # BHHB and level-k plans
+                plan.txv_block(h.contiguous(), x.contiguous(), y)
+            else:
+                plan.txv(h.contiguous(), x.contiguous(), y)
             ctx.save_for_backward(h, x)
             ctx.plan = plan
             return y

@@ -226,3 +226,27 @@ def test_level3_full_size(dev):
         ref = lv.fast_level_y(S, [Xs[2 * t], Xs[2 * t + 1]], sizes)
         assert rel(lv.unvec(y[t * n:(t + 1) * n], (22, 22, 22)), ref) <= 1e-5, t
     plan.close()
+
+
+def test_autograd_through_a_level3_plan(dev):
+    # torch.autograd through HankelTxV on a level-k plan: the gradients of a
+    # real loss equal the oracle's adjoint (complex128)
+    sizes = [[5, 4, 3], [3, 2, 2], [2, 3, 2]]
+    Gs, Xss, h, x, d, ny = pack(sizes, 1, seed=11, cplx=True)
+    plan = hk.Plan(d, hk.C128, 0)
+    H = torch.tensor(h, dtype=torch.complex128, device=dev, requires_grad=True)
+    X = torch.tensor(x, dtype=torch.complex128, device=dev, requires_grad=True)
+    rng = np.random.default_rng(4)
+    w = torch.tensor(rng.standard_normal(ny) + 1j * rng.standard_normal(ny), device=dev)
+    y = hk.hankel_txv_autograd(H, X, plan)
+    loss = (w.conj() * y).real.sum()  # dL/dy (PyTorch convention) is w
+    loss.backward()
+    torch.cuda.synchronize()
+    shape = lv.mode_shape(sizes, 0)
+    rG, rX = lv.fast_level_grads(Gs[0], Xss[0][1:], sizes, lv.unvec(w.cpu().numpy(), shape))
+    assert rel(lv.unvec(H.grad.cpu().numpy(), rG.shape), rG) <= 1e-12
+    for p in range(1, 3):
+        o = d["x_off"][0][p]
+        got = lv.unvec(X.grad.cpu().numpy()[o: o + rX[p - 1].size], rX[p - 1].shape)
+        assert rel(got, rX[p - 1]) <= 1e-12, p
+    plan.close()

@@ -46,7 +46,7 @@ def worker(rank, world, port, out):
 
 def test_two_gloo_ranks_weak_scaling():
     world = 2
-    manager = mp.Manager()
+    manager = mp.get_context("spawn").Manager()
     out = manager.dict()
     mp.spawn(worker, args=(world, free_port(), out), nprocs=world, join=True)
     (d0, s0, t0, r0), (d1, s1, t1, r1) = out[0], out[1]

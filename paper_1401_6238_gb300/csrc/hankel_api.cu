@@ -613,10 +613,30 @@ void desc_ranges(const hankel_desc& d, uint32_t flags, int64_t r[6]) {
 
 // Split a plan's descriptors into contiguous ranges with one sub-plan each
 // (made once, on the first pipelined hankel_txv_host).
-hankel_status build_chunks(hankel_plan_s* p, int nchunks) {
+hankel_status build_chunks(hankel_plan_s* p) {
     const int64_t count = (int64_t)p->descs.size();
+    // Range sizes by input bytes: small at both ends, so that the first copy
+    // in (which nothing overlaps) and the last range's kernels and copy out
+    // (which overlap nothing) are short; each middle range's kernels finish
+    // while the next range is still being copied in.
+    static const double kShare[] = {0.04, 0.12, 0.20, 0.24, 0.20, 0.12, 0.08};
+    constexpr int nchunks = (int)(sizeof(kShare) / sizeof(kShare[0]));
+    std::vector<double> cum(count + 1, 0.0);
+    for (int64_t i = 0; i < count; ++i) {
+        int64_t r[6];
+        desc_ranges(p->descs[i], p->flags, r);
+        cum[i + 1] = cum[i] + (double)(r[1] - r[0]) + (double)(r[3] - r[2]);
+    }
+    std::vector<int64_t> cut(nchunks + 1, count);
+    cut[0] = 0;
+    double acc = 0.0;
+    for (int c = 1; c < nchunks; ++c) {
+        acc += kShare[c - 1];
+        cut[c] = std::lower_bound(cum.begin(), cum.end(), acc * cum[count]) - cum.begin();
+        cut[c] = std::max(cut[c], cut[c - 1]);
+    }
     for (int c = 0; c < nchunks; ++c) {
-        const int64_t c0 = count * c / nchunks, c1 = count * (c + 1) / nchunks;
+        const int64_t c0 = cut[c], c1 = std::min<int64_t>(cut[c + 1], count);
         if (c1 <= c0) continue;
         hankel_plan_s::Chunk ch{nullptr, c0, INT64_MAX, 0, INT64_MAX, 0, INT64_MAX, 0};
         for (int64_t i = c0; i < c1; ++i) {
@@ -911,11 +931,10 @@ hankel_status hankel_txv_host(hankel_plan_t p, const void* h, const void* x, voi
     // Large batches run as a pipeline of contiguous descriptor ranges: the
     // copies in of range c + 1 and the copy out of range c - 1 overlap the
     // kernels of range c.
-    constexpr int kChunks = 4;
-    const bool pipe = p->from_descs && (int64_t)p->descs.size() >= 32 * kChunks && hb + xb >= (8u << 20);
+    const bool pipe = p->from_descs && (int64_t)p->descs.size() >= 256 && hb + xb >= (8u << 20);
     if (pipe && !p->chunks_tried) {
         p->chunks_tried = true;
-        if (build_chunks(p, kChunks) != HANKEL_OK) {
+        if (build_chunks(p) != HANKEL_OK) {
             for (auto& c : p->chunks) free_plan(c.plan);
             p->chunks.clear();
         }

@@ -217,10 +217,14 @@ hankel_status hankel_txv(hankel_plan_t plan, const void* h, const void* x, void*
                          hankel_stream_t stream);
 
 /*
- * hankel_txv_host -- hankel_txv on HOST buffers: copies h and x to plan-owned
- * device staging buffers, computes, copies y / alpha back, all queued on
- * `stream`; returns after the stream has finished (the host buffers are
- * ready).  Pinned host memory makes the copies asynchronous DMA.  The first
+ * hankel_txv_host -- hankel_txv on HOST buffers; returns after `stream` has
+ * finished (the host buffers are ready).  When every buffer is page-locked
+ * memory mapped into the device address space (cudaHostAlloc /
+ * cudaHostRegister, as cudaPointerGetAttributes reports), the kernels read
+ * and write the host buffers directly across the host link.  Otherwise h and
+ * x are copied to plan-owned device staging buffers and y / alpha back, all
+ * queued on `stream`; large batches are pipelined over descriptor ranges
+ * (sub-plans whose copies overlap each other's kernels).  The first staged
  * call allocates the staging buffers (they live until hankel_plan_destroy).
  * Errors: as hankel_txv, plus ENOMEM.
  */

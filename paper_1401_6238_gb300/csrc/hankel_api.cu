@@ -588,6 +588,17 @@ hankel_status build_multi_path(hankel_plan_s* p) {
     return make_streams(p, opl ? 0 : p->multi_launches.size());
 }
 
+// Device address of page-locked host memory that is mapped into the device
+// address space, or nullptr for any other pointer.
+const void* mapped_host(const void* ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return (a.type == cudaMemoryTypeHost) ? a.devicePointer : nullptr;
+}
+
 // Element ranges of h, x and y that one descriptor reads or writes.
 void desc_ranges(const hankel_desc& d, uint32_t flags, int64_t r[6]) {
     const bool block = flags & HANKEL_BLOCK, anti = flags & HANKEL_ANTICIRCULANT;
@@ -915,6 +926,22 @@ hankel_status hankel_txv_host(hankel_plan_t p, const void* h, const void* x, voi
     if (!p) return fail(HANKEL_EINVAL, "plan is NULL");
     if (!h || !x) return fail(HANKEL_EINVAL, "h and x must be host pointers");
     if (!y && !alpha) return fail(HANKEL_EINVAL, "nothing to compute: y and alpha are both NULL");
+    {
+        // page-locked host memory mapped into the device address space: the
+        // kernels read the inputs and write the outputs across the host link
+        // directly, with no staging copies
+        const void* dh = mapped_host(h);
+        const void* dx = mapped_host(x);
+        void* dy = y ? const_cast<void*>(mapped_host(y)) : nullptr;
+        void* da = alpha ? const_cast<void*>(mapped_host(alpha)) : nullptr;
+        if (dh && dx && (!y || dy) && (!alpha || da)) {
+            const hankel_status s = (p->flags & HANKEL_BLOCK) ? hankel_txv_block(p, dh, dx, dy, da, stream)
+                                                              : hankel_txv(p, dh, dx, dy, da, stream);
+            if (s != HANKEL_OK) return s;
+            const cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+            return e == cudaSuccess ? HANKEL_OK : cuda_fail(e, "stream synchronize");
+        }
+    }
     const size_t es = elem_size(p->dtype);
     const size_t hb = (size_t)std::max<int64_t>(p->h_elems, 1) * es;
     const size_t xb = (size_t)std::max<int64_t>(p->x_elems, 1) * es;

@@ -44,13 +44,15 @@ def test_full_batch_host_matches_device(dev):
     assert np.abs(ah.numpy() - A.cpu().numpy()).max() <= 1e-5 * np.abs(A.cpu().numpy()).max()
     # again: other buffers (an eager run), then the same buffers twice (the
     # pipeline replays as a captured graph) with fresh inputs in place
+    # (zeros_like is not page-locked: these calls stage through copies, with
+    # other job pairings, so they agree to rounding, not bit for bit)
     yh2 = torch.zeros_like(yh)
     plan.txv_host(hh, xh, yh2, None)
-    assert torch.equal(yh2, yh)
+    per_tensor_close(yh2.numpy(), yh.numpy(), b.y_off, b.dims, 1e-5)
     # alpha alone
     ah2 = torch.zeros_like(ah)
     plan.txv_host(hh, xh, None, ah2)
-    assert torch.equal(ah2, ah)
+    assert np.abs(ah2.numpy() - ah.numpy()).max() <= 1e-5 * np.abs(ah.numpy()).max()
     for scale in (2.0, 0.5):
         hh.mul_(scale)
         yh.zero_()

@@ -174,6 +174,10 @@ struct hankel_plan_s {
     std::vector<hankel_desc> descs;
     std::vector<int> Lof;
     bool real_path = false;
+    // descriptors whose h or x regions overlap: the fused real path writes
+    // gradients per tensor, so their adjoint runs on the general path (which
+    // sums over every use)
+    bool shared_io = false;
     // fused path for real tensors with a different vector per mode
     bool multi_path = false;
     std::vector<hk::MultiJob> multi_jobs;
@@ -214,6 +218,16 @@ struct hankel_plan_s {
     cudaGraphExec_t graph = nullptr;
     const void* gkey[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t cap_in = nullptr, cap_out = nullptr;
+    // anti-circulant tensors of dimensions the transforms do not cover: the
+    // Hankel plan `inner` of the periodic generating vectors, expanded from
+    // the caller's c into ws_h before each call (gradients folded back)
+    hankel_plan_s* inner = nullptr;
+    std::vector<hk::ExpandEntry> expand;
+    std::vector<hk::FoldGroup> folds;
+    hk::ExpandEntry* d_expand = nullptr;
+    hk::FoldGroup* d_folds = nullptr;
+    int max_d = 0, max_n = 0;
+    void *ws_h = nullptr, *ws_gh = nullptr;
 };
 
 namespace {
@@ -240,6 +254,11 @@ void free_plan(hankel_plan_s* p) {
     if (p->cap_in) cudaEventDestroy(p->cap_in);
     if (p->cap_out) cudaEventDestroy(p->cap_out);
     for (auto ev : p->pipe_events) cudaEventDestroy(ev);
+    if (p->inner) free_plan(p->inner);
+    cudaFree(p->d_expand);
+    cudaFree(p->d_folds);
+    cudaFree(p->ws_h);
+    cudaFree(p->ws_gh);
     if (p->gen) hk::general_destroy(p->gen);
     delete p;
 }
@@ -756,6 +775,89 @@ void capture_pipeline(hankel_plan_s* p, const void* h, const void* x, void* y, v
     if (graph) cudaGraphDestroy(graph);
 }
 
+// Whether an anti-circulant plan needs the periodic expansion: some
+// dimension n is not one of the transform lengths.
+bool needs_expansion(const hankel_desc* descs, int64_t count) {
+    for (int64_t i = 0; i < count; ++i)
+        if (descs[i].n[0] >= 2 && (lengths().find(descs[i].n[0]) == nullptr || descs[i].n[0] > kMaxL)) return true;
+    return false;
+}
+
+hankel_status plan_expanded(hankel_plan_t* out, const hankel_desc* descs, int64_t count, hankel_dtype dtype,
+                            uint32_t flags) {
+    std::vector<hankel_desc> in(descs, descs + count);
+    auto* p = new (std::nothrow) hankel_plan_s;
+    if (!p) return fail(HANKEL_ENOMEM, "host allocation failed");
+    p->dtype = dtype;
+    p->flags = flags;
+    cudaGetDevice(&p->device);
+    p->descs.assign(descs, descs + count);
+    std::map<std::pair<int64_t, int>, std::vector<int>> groups;
+    int64_t ws = 0;
+    for (int64_t i = 0; i < count; ++i) {
+        const hankel_desc& D = descs[i];
+        for (int q = 1; q < D.m; ++q)
+            if (D.n[q] != D.n[0]) {
+                free_plan(p);
+                return fail(HANKEL_EINVAL, "descriptor %lld: anti-circulant tensors are square", (long long)i);
+            }
+        if (D.n[0] < 2) {
+            free_plan(p);
+            return fail(HANKEL_EINVAL, "descriptor %lld: anti-circulant dimension n=%d must be >= 2", (long long)i,
+                        D.n[0]);
+        }
+        const int64_t d = (int64_t)D.m * (D.n[0] - 1) + 1;
+        const LenInfo* li = lengths().pick(d);
+        if (!li || li->L > kMaxL) {
+            free_plan(p);
+            return fail(HANKEL_EUNSUPPORTED, "descriptor %lld: anti-circulant dimension n=%d is not an FFT length "
+                        "and its periodic embedding d=%lld exceeds the maximum FFT length %lld",
+                        (long long)i, D.n[0], (long long)d, (long long)kMaxL);
+        }
+        p->expand.push_back({D.h_off, ws, D.n[0], (int32_t)d});
+        groups[std::make_pair(D.h_off, D.n[0])].push_back((int)i);
+        in[i].h_off = ws;
+        ws += (d + 3) / 4 * 4;
+        p->max_d = std::max<int>(p->max_d, (int)d);
+        p->max_n = std::max<int>(p->max_n, D.n[0]);
+        p->h_elems = std::max<int64_t>(p->h_elems, D.h_off + D.n[0]);
+    }
+    // fold groups: entries sharing c, listed contiguously
+    std::vector<hk::ExpandEntry> ordered;
+    for (auto& kv : groups) {
+        hk::FoldGroup G{kv.first.first, kv.first.second, (int32_t)ordered.size(), (int32_t)kv.second.size()};
+        for (int i : kv.second) ordered.push_back(p->expand[i]);
+        p->folds.push_back(G);
+    }
+    hankel_status s = hankel_plan(&p->inner, in.data(), count, dtype, flags & ~(uint32_t)HANKEL_ANTICIRCULANT);
+    if (s != HANKEL_OK) { free_plan(p); return s; }
+    const size_t es = elem_size(dtype);
+    cudaError_t e;
+    if ((e = cudaMalloc(&p->ws_h, std::max<int64_t>(ws, 1) * es)) != cudaSuccess) { free_plan(p); return cuda_fail(e, "cudaMalloc(expansion)"); }
+    if ((e = cudaMalloc(&p->ws_gh, std::max<int64_t>(ws, 1) * es)) != cudaSuccess) { free_plan(p); return cuda_fail(e, "cudaMalloc(expansion)"); }
+    if ((e = cudaMalloc(&p->d_expand, p->expand.size() * sizeof(hk::ExpandEntry))) != cudaSuccess) { free_plan(p); return cuda_fail(e, "cudaMalloc(expansion)"); }
+    if ((e = cudaMalloc(&p->d_folds, p->folds.size() * sizeof(hk::FoldGroup) + ordered.size() * sizeof(hk::ExpandEntry))) != cudaSuccess) { free_plan(p); return cuda_fail(e, "cudaMalloc(expansion)"); }
+    e = cudaMemcpy(p->d_expand, p->expand.data(), p->expand.size() * sizeof(hk::ExpandEntry), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p->d_folds, p->folds.data(), p->folds.size() * sizeof(hk::FoldGroup), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(reinterpret_cast<char*>(p->d_folds) + p->folds.size() * sizeof(hk::FoldGroup), ordered.data(),
+                       ordered.size() * sizeof(hk::ExpandEntry), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { free_plan(p); return cuda_fail(e, "cudaMemcpy(expansion)"); }
+    p->x_elems = p->inner->x_elems;
+    p->y_elems = p->inner->y_elems;
+    p->sum_L = p->inner->sum_L;
+    p->max_L = p->inner->max_L;
+    *out = p;
+    return HANKEL_OK;
+}
+
+// The fold groups' entries (ordered by group) follow the groups in d_folds.
+const hk::ExpandEntry* fold_entries(const hankel_plan_s* p) {
+    return reinterpret_cast<const hk::ExpandEntry*>(reinterpret_cast<const char*>(p->d_folds) +
+                                                    p->folds.size() * sizeof(hk::FoldGroup));
+}
+
 // The general-path program of a plan (made on first use for plans whose
 // forward products run on a fused path but whose adjoint runs here).
 hankel_status ensure_general(hankel_plan_s* p) {
@@ -764,7 +866,27 @@ hankel_status ensure_general(hankel_plan_s* p) {
     std::vector<hankel_mdesc> md(p->descs.size());
     for (size_t i = 0; i < p->descs.size(); ++i) md[i] = to_levels(p->descs[i], block);
     int64_t he, xe, ye, sl, ml;
-    return hk::general_create(&p->gen, md, p->dtype, p->flags, &he, &xe, &ye, &sl, &ml, g_err);
+    // its forward never runs, so it keeps no spectra for the adjoint
+    return hk::general_create(&p->gen, md, p->dtype, p->flags & ~(uint32_t)HANKEL_STORE_SPECTRA, &he, &xe, &ye, &sl,
+                              &ml, g_err);
+}
+
+// Whether any two descriptors' h regions, or any two x regions, overlap.
+bool regions_overlap(const std::vector<hankel_desc>& descs, uint32_t flags) {
+    std::vector<std::pair<int64_t, int64_t>> hs, xs;
+    for (const auto& d : descs) {
+        int64_t r[6];
+        desc_ranges(d, flags, r);
+        hs.emplace_back(r[0], r[1]);
+        const int nx = (flags & HANKEL_SAME_X) ? 1 : d.m;
+        for (int q = 0; q < nx; ++q) xs.emplace_back(d.x_off[q], d.x_off[q] + d.n[q]);
+    }
+    for (auto* v : {&hs, &xs}) {
+        std::sort(v->begin(), v->end());
+        for (size_t i = 1; i < v->size(); ++i)
+            if ((*v)[i].first < (*v)[i - 1].second) return true;
+    }
+    return false;
 }
 
 }  // namespace
@@ -778,6 +900,14 @@ hankel_status hankel_plan(hankel_plan_t* out, const hankel_desc* descs, int64_t 
     if (descs == nullptr || count < 1) return fail(HANKEL_EINVAL, "need at least one descriptor");
     if (dtype < HANKEL_R32 || dtype > HANKEL_C128) return fail(HANKEL_EINVAL, "unknown dtype %d", (int)dtype);
     if (flags & ~(uint32_t)0x3F) return fail(HANKEL_EINVAL, "unknown flag bits 0x%x", flags);
+    if ((flags & HANKEL_ANTICIRCULANT) && !(flags & HANKEL_BLOCK) && needs_expansion(descs, count)) {
+        for (int64_t i = 0; i < count; ++i) {
+            int64_t d;
+            const hankel_status s = validate(descs[i], i, flags, d);
+            if (s != HANKEL_OK) return s;
+        }
+        return plan_expanded(out, descs, count, dtype, flags);
+    }
     auto* p = new (std::nothrow) hankel_plan_s;
     if (!p) return fail(HANKEL_ENOMEM, "host allocation failed");
     p->dtype = dtype;
@@ -833,6 +963,7 @@ hankel_status hankel_plan(hankel_plan_t* out, const hankel_desc* descs, int64_t 
         for (auto& D : p->descs)
             for (int q = 1; q < D.m; ++q) square = square && D.n[q] == D.n[0];
     p->real_path = !block && !is_complex(dtype) && (flags & HANKEL_SAME_X) && square;
+    if (p->real_path) p->shared_io = regions_overlap(p->descs, flags);
     // real tensors with a vector per mode: the fused m + 1 transform kernel
     // when every length fits its three shared buffers
     p->multi_path = !block && !is_complex(dtype) && !(flags & (HANKEL_SAME_X | HANKEL_STORE_SPECTRA)) &&
@@ -911,6 +1042,12 @@ hankel_status hankel_txv(hankel_plan_t p, const void* h, const void* x, void* y,
     if (!y && !alpha) return fail(HANKEL_EINVAL, "nothing to compute: y and alpha are both NULL");
     cudaStream_t st = (cudaStream_t)stream;
     const bool dbl = is_double(p->dtype);
+    if (p->inner) {
+        const cudaError_t e = hk::launch_expand((int)elem_size(p->dtype), p->d_expand, (int)p->expand.size(), p->max_d,
+                                                h, p->ws_h, st);
+        if (e != cudaSuccess) return cuda_fail(e, "expansion kernel");
+        return hankel_txv(p->inner, p->ws_h, x, y, alpha, stream);
+    }
     if (p->multi_path)
         return run_forked(p, p->multi_launches, st, [&](const hk::RealLaunch& lc, cudaStream_t s) {
             return hk::launch_real_multi(dbl, lc, p->d_multi, h, x, y, alpha, p->d_tw, s);
@@ -1016,10 +1153,23 @@ hankel_status hankel_txv_backward(hankel_plan_t p, const void* grad_y, const voi
     if (!grad_y || !h || !x) return fail(HANKEL_EINVAL, "grad_y, h and x must be device pointers");
     if (!grad_h && !grad_x) return fail(HANKEL_EINVAL, "nothing to compute: grad_h and grad_x are both NULL");
     cudaStream_t st = (cudaStream_t)stream;
-    if (p->multi_path) {
-        // the adjoint of the distinct-vector products runs on the general path
+    if (p->inner) {
+        cudaError_t e = hk::launch_expand((int)elem_size(p->dtype), p->d_expand, (int)p->expand.size(), p->max_d, h,
+                                          p->ws_h, st);
+        if (e != cudaSuccess) return cuda_fail(e, "expansion kernel");
+        const hankel_status s =
+            hankel_txv_backward(p->inner, grad_y, p->ws_h, x, grad_h ? p->ws_gh : nullptr, grad_x, stream);
+        if (s != HANKEL_OK || !grad_h) return s;
+        e = hk::launch_fold(is_double(p->dtype), is_complex(p->dtype), fold_entries(p), p->d_folds,
+                            (int)p->folds.size(), p->max_n, p->ws_gh, grad_h, st);
+        return e == cudaSuccess ? HANKEL_OK : cuda_fail(e, "fold kernel");
+    }
+    if (p->multi_path || (p->real_path && p->shared_io)) {
+        // the adjoint of the distinct-vector products, and of fused plans
+        // whose tensors share h or x storage, runs on the general path
         const hankel_status s = ensure_general(p);
         if (s != HANKEL_OK) return s;
+        return hk::general_backward(p->gen, grad_y, h, x, grad_h, grad_x, st, g_err);
     }
     if (!p->real_path) return hk::general_backward(p->gen, grad_y, h, x, grad_h, grad_x, st, g_err);
     const bool dbl = is_double(p->dtype);
@@ -1039,7 +1189,14 @@ hankel_status hankel_plan_query(hankel_plan_t p, hankel_plan_info* info) {
     info->h_elems = p->h_elems;
     info->x_elems = p->x_elems;
     info->y_elems = p->y_elems;
-    if (p->multi_path) {
+    if (p->inner) {
+        hankel_plan_info in;
+        hankel_plan_query(p->inner, &in);
+        info->jobs = in.jobs;
+        info->launches = in.launches + 1;
+        info->distinct_lengths = in.distinct_lengths;
+        info->workspace_bytes = in.workspace_bytes;
+    } else if (p->multi_path) {
         info->jobs = (int64_t)p->multi_jobs.size();
         info->launches = (int64_t)p->multi_launches.size();
         info->distinct_lengths = (int64_t)p->tw_off.size();

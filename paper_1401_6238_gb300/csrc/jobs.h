@@ -58,6 +58,20 @@ struct MultiJob {
     int64_t xA[HANKEL_MAX_ORDER], xB[HANKEL_MAX_ORDER];
 };
 
+// Anti-circulant tensor whose dimension n the transforms do not cover, run as
+// the Hankel tensor of its periodic generating vector h_k = c[k mod n],
+// k < d = m (n - 1) + 1, expanded from c (at c_off) into a workspace (at
+// ws_off).  Gradients fold back: grad_c[j] = sum over k = j mod n of grad_h[k],
+// summed over every entry of one fold group (entries that share c).
+struct ExpandEntry {
+    int64_t c_off, ws_off;
+    int32_t n, d;
+};
+struct FoldGroup {
+    int64_t c_off;
+    int32_t n, first, count;  // entries [first, first + count) of the expansion table
+};
+
 // Launch of one group of jobs that share a block size.
 struct RealLaunch {
     int32_t first, count;  // range in the job table

@@ -25,6 +25,11 @@ cudaError_t launch_real_backward(bool dbl, const RealLaunch& lc, const RealJob* 
 cudaError_t launch_real_multi(bool dbl, const RealLaunch& lc, const MultiJob* jobs, const void* h, const void* x,
                               void* y, void* alpha, const void* tw, cudaStream_t st);
 cudaError_t launch_twiddles(bool dbl, void* out, int L, cudaStream_t st);
+// periodic expansion of anti-circulant generating vectors and the fold of
+// their gradients (elem: bytes per element of the plan's dtype; cplx: complex)
+cudaError_t launch_expand(int elem, const ExpandEntry* e, int count, int max_d, const void* c, void* h, cudaStream_t st);
+cudaError_t launch_fold(bool dbl, bool cplx, const ExpandEntry* e, const FoldGroup* g, int ngroups, int max_n,
+                        const void* gh, void* gc, cudaStream_t st);
 // per-pass twiddle layout of fft_stage.cuh (real-data kernels)
 cudaError_t launch_stage_twiddles(bool dbl, void* out, const FftPlan& P, cudaStream_t st);
 int stage_twiddle_count(const FftPlan& P);

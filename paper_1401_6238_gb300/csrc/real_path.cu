@@ -21,6 +21,7 @@
 // reversed) and grad_x (imaginary part).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -630,6 +631,69 @@ __global__ void __launch_bounds__(512) split_backward_kernel(const RealJob* __re
     g.sync();
     const AdjSt<T> st{gh ? gh + J.hA : nullptr, J.dA, gx ? gx + J.xA : nullptr, J.nA, L};
     fft_stage<T>(J.P, GLd<T>{nullptr, 0, nullptr, 0}, sm.b0, sm.b1, sm.b0, SplitAdjSt<T>{st, c}, false, sm.twM, g);
+}
+
+// ------------------------------------------------ anti-circulant expansion
+
+struct alignas(16) Bytes16 {
+    unsigned long long a, b;
+};
+
+template <typename E>
+__global__ void expand_kernel(const ExpandEntry* __restrict__ e, int count, const E* __restrict__ c, E* h) {
+    for (int t = blockIdx.y; t < count; t += gridDim.y) {
+        const ExpandEntry x = e[t];
+        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < x.d; k += gridDim.x * blockDim.x)
+            h[x.ws_off + k] = c[x.c_off + (k % x.n)];
+    }
+}
+
+template <typename V>
+__global__ void fold_kernel(const ExpandEntry* __restrict__ e, const FoldGroup* __restrict__ groups, int ngroups,
+                            const V* __restrict__ gh, V* gc) {
+    for (int gi = blockIdx.y; gi < ngroups; gi += gridDim.y) {
+        const FoldGroup G = groups[gi];
+        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < G.n; j += gridDim.x * blockDim.x) {
+            V acc = gh[e[G.first].ws_off + j];
+            bool first = true;
+            for (int t = G.first; t < G.first + G.count; ++t) {
+                const ExpandEntry x = e[t];
+                for (int k = j; k < x.d; k += G.n) {
+                    if (first) {
+                        first = false;
+                        continue;  // the first term initialised acc
+                    }
+                    acc = acc + gh[x.ws_off + k];
+                }
+            }
+            gc[G.c_off + j] = acc;
+        }
+    }
+}
+
+cudaError_t launch_expand(int elem, const ExpandEntry* e, int count, int max_d, const void* c, void* h,
+                          cudaStream_t st) {
+    const dim3 grid((unsigned)std::min(64, (max_d + 255) / 256), (unsigned)std::min(count, 65535));
+    switch (elem) {
+        case 4: expand_kernel<float><<<grid, 256, 0, st>>>(e, count, (const float*)c, (float*)h); break;
+        case 8: expand_kernel<double><<<grid, 256, 0, st>>>(e, count, (const double*)c, (double*)h); break;
+        default: expand_kernel<Bytes16><<<grid, 256, 0, st>>>(e, count, (const Bytes16*)c, (Bytes16*)h); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fold(bool dbl, bool cplx, const ExpandEntry* e, const FoldGroup* g, int ngroups, int max_n,
+                        const void* gh, void* gc, cudaStream_t st) {
+    const dim3 grid((unsigned)std::min(64, (max_n + 255) / 256), (unsigned)std::min(ngroups, 65535));
+    if (cplx && dbl)
+        fold_kernel<cx<double>><<<grid, 256, 0, st>>>(e, g, ngroups, (const cx<double>*)gh, (cx<double>*)gc);
+    else if (cplx)
+        fold_kernel<cx<float>><<<grid, 256, 0, st>>>(e, g, ngroups, (const cx<float>*)gh, (cx<float>*)gc);
+    else if (dbl)
+        fold_kernel<double><<<grid, 256, 0, st>>>(e, g, ngroups, (const double*)gh, (double*)gc);
+    else
+        fold_kernel<float><<<grid, 256, 0, st>>>(e, g, ngroups, (const float*)gh, (float*)gc);
+    return cudaGetLastError();
 }
 
 // Two-level twiddle table of length L (fft_stage.cuh): A[j] = w_L^{64 j},

@@ -194,3 +194,89 @@ def test_block_anticirculant(dev):
     assert torch.equal(Y3, Y)
     plan.close()
     plan3.close()
+
+
+@pytest.mark.parametrize("dtype,tol", [(hk.R64, 1e-12), (hk.R32, 1e-5)])
+def test_dimensions_without_a_transform_length(dev, dtype, tol):
+    # n prime (or with a factor above 7): the library runs the Hankel tensor
+    # of the periodic generating vector instead; forward, alpha and adjoint
+    rng = np.random.default_rng(7)
+    cases = [(3, 11), (2, 97), (4, 1021), (3, 13)]
+    cs = [rng.standard_normal(n) / np.sqrt(n) for m, n in cases]
+    xs = [rng.standard_normal(n) / np.sqrt(n) for m, n in cases]
+    offs = np.cumsum([0] + [n for m, n in cases])[:-1]
+    d = hk.square_descs([m for m, n in cases], [n for m, n in cases], offs, offs, offs)
+    plan = hk.Plan(d, dtype, hk.SAME_X | hk.ANTICIRCULANT)
+    total = int(offs[-1] + cases[-1][1])
+    H, X = t_(np.concatenate(cs), dtype, dev), t_(np.concatenate(xs), dtype, dev)
+    Y = torch.zeros(total, dtype=TDT[dtype], device=dev)
+    A = torch.zeros(len(cases), dtype=TDT[dtype], device=dev)
+    plan.txv(H, X, Y, A)
+    g = rng.standard_normal(total)
+    gh, gx = torch.zeros_like(H), torch.zeros_like(X)
+    plan.backward(t_(g, dtype, dev), H, X, gh, gx)
+    torch.cuda.synchronize()
+    y, a, gh, gx = Y.cpu().numpy(), A.cpu().numpy(), gh.cpu().numpy(), gx.cpu().numpy()
+    for i, (m, n) in enumerate(cases):
+        o = offs[i]
+        ref = oracle.fast_y(periodic(cs[i], m), [xs[i]] * (m - 1), [n] * m).real
+        assert rel(y[o:o + n], ref) <= tol, (m, n)
+        ar = oracle.fast_alpha(periodic(cs[i], m), [xs[i]] * m, [n] * m).real
+        assert abs(a[i] - ar) <= tol * np.abs(ref).max() * np.abs(xs[i]).sum(), (m, n)
+        rh, rxs = oracle.fast_grads(periodic(cs[i], m), [xs[i]] * (m - 1), [n] * m, g[o:o + n])
+        fold = np.zeros(n)
+        np.add.at(fold, np.arange(rh.shape[0]) % n, rh.real)
+        assert rel(gh[o:o + n], fold) <= 10 * tol, (m, n)
+        assert rel(gx[o:o + n], sum(r.real for r in rxs)) <= 10 * tol, (m, n)
+    plan.close()
+
+
+def test_shared_compressed_vector_gradients_are_summed(dev):
+    # two complex products of one c (n = 11) with distinct vectors: the
+    # gradient with respect to c is the sum of both folds
+    rng = np.random.default_rng(8)
+    cr = lambda n: rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    m, n = 3, 11
+    c = cr(n)
+    vs = [cr(n) for _ in range(6)]
+    d = hk.make_descs(2)
+    for t in range(2):
+        d[t]["m"] = m
+        d[t]["n"][:m] = n
+        d[t]["h_off"] = 0
+        d[t]["x_off"][:m] = [(3 * t + p) * n for p in range(m)]
+        d[t]["y_off"] = t * n
+    plan = hk.Plan(d, hk.C128, hk.ANTICIRCULANT)
+    g = cr(2 * n)
+    gh = torch.zeros(n, dtype=torch.complex128, device=dev)
+    gx = torch.zeros(6 * n, dtype=torch.complex128, device=dev)
+    Y = torch.zeros(2 * n, dtype=torch.complex128, device=dev)
+    plan.txv(t_(c, hk.C128, dev), t_(np.concatenate(vs), hk.C128, dev), Y)
+    plan.backward(t_(g, hk.C128, dev), t_(c, hk.C128, dev), t_(np.concatenate(vs), hk.C128, dev), gh, gx)
+    torch.cuda.synchronize()
+    fold = np.zeros(n, complex)
+    y = Y.cpu().numpy()
+    for t in range(2):
+        ref = oracle.fast_y(periodic(c, m), vs[3 * t + 1: 3 * t + 3], [n] * m)
+        assert rel(y[t * n:(t + 1) * n], ref) <= 1e-12
+        rh, rxs = oracle.fast_grads(periodic(c, m), vs[3 * t + 1: 3 * t + 3], [n] * m, g[t * n:(t + 1) * n])
+        np.add.at(fold, np.arange(rh.shape[0]) % n, rh)
+        for p in (1, 2):
+            o = (3 * t + p) * n
+            assert rel(gx.cpu().numpy()[o:o + n], rxs[p - 1]) <= 1e-12, (t, p)
+    assert rel(gh.cpu().numpy(), fold) <= 1e-12
+    plan.close()
+
+
+def test_corollary_2_2_for_odd_n(dev):
+    # odd n: the all-ones eigenpair, through the periodic embedding
+    n, m = 11, 4
+    c = np.random.default_rng(9).standard_normal(n)
+    d = hk.square_descs([m], [n], [0], [0], [0])
+    plan = hk.Plan(d, hk.R64, hk.SAME_X | hk.ANTICIRCULANT)
+    Y = torch.zeros(n, dtype=torch.float64, device=dev)
+    plan.txv(t_(c, hk.R64, dev), t_(np.ones(n), hk.R64, dev), Y)
+    torch.cuda.synchronize()
+    lam = n ** (m - 2) * c.sum()
+    assert np.abs(Y.cpu().numpy() - lam).max() <= 1e-12 * abs(lam)
+    plan.close()

@@ -163,10 +163,12 @@ def test_multilevel_rejects_other_flags(lib):
 
 
 def test_anticirculant_needs_square_tensors_and_fft_lengths(lib):
-    d = hk.square_descs([3], [11], [0], [0], [0])  # 11 is prime: no transform of that length
+    # 10007 is prime (no transform of that length) and its periodic
+    # embedding, d = 3 * 10006 + 1, exceeds the longest transform
+    d = hk.square_descs([3], [10007], [0], [0], [0])
     with pytest.raises(hk.HankelError) as e:
         hk.hankel_plan(d, hk.R32, hk.SAME_X | hk.ANTICIRCULANT)
-    assert e.value.status == hk.EUNSUPPORTED and "n=11" in e.value.message
+    assert e.value.status == hk.EUNSUPPORTED and "n=10007" in e.value.message
     d = hk.make_descs(1)
     d["m"] = 3
     d["n"][0, :3] = [8, 8, 6]

@@ -88,9 +88,13 @@ enum {
      * tensors of Section 2.2).  h holds the compressed generating vector c
      * (length n; block plans: the compressed generating array, column-major)
      * and the products of Section 3 run at FFT length exactly n (Theorem
-     * 2.1), so n must be one of this build's FFT lengths
-     * (hankel_fft_length(n) == n, a 2,3,5,7-smooth length), else
-     * HANKEL_EUNSUPPORTED.  y has n entries per level. */
+     * 2.1) when n is one of this build's FFT lengths (hankel_fft_length(n)
+     * == n, a 2,3,5,7-smooth length).  For other n (one-level plans) the
+     * tensor runs as the Hankel tensor of its periodic generating vector
+     * c[k mod n], k < m (n - 1) + 1, expanded in plan workspace;
+     * HANKEL_EUNSUPPORTED when that embedding exceeds the longest transform
+     * (block and level-k plans: whenever a dimension is not a transform
+     * length).  y has n entries per level. */
     HANKEL_ANTICIRCULANT = 1u << 5
 };
 

@@ -24,6 +24,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -500,8 +501,9 @@ def main():
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    clk_path = os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks.csv"
+    # per-run clock samples; BENCH_CLOCKS_CSV keeps them at a chosen path
+    clk_path = os.environ.get("BENCH_CLOCKS_CSV") or os.path.join(
+        tempfile.gettempdir(), "bench_clocks_%d.csv" % os.getpid())
     sampler = start_clock_sampler(clk_path) if rank == 0 else None
     time.sleep(0.3 if sampler else 0)
     torch.cuda.synchronize()

@@ -185,9 +185,9 @@ __global__ void __launch_bounds__(512) line_kernel(const LineTask* __restrict__ 
 // other groups of its warp (__syncwarp over the lanes that hold a line: the
 // groups of a warp run the same pass sequence), so a warp keeps 32 / gth
 // lines in flight instead of one line with mostly idle lanes.  The block
-// loads the twiddle table once.
+// loads the twiddle table once.  Built for three resident blocks per SM.
 template <typename T>
-__global__ void __launch_bounds__(256) line_group_kernel(const LineTask* __restrict__ tasks, int first, int count,
+__global__ void __launch_bounds__(256, 3) line_group_kernel(const LineTask* __restrict__ tasks, int first, int count,
                                                          int lpb, int gth, const void* __restrict__ in, void* out,
                                                          cx<T>* ws, const cx<T>* __restrict__ tw_all, int L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -656,8 +656,11 @@ cudaError_t run_lines(GeneralPlan* g, const Launch& l, const LineTask* d_tasks, 
                       cudaStream_t st) {
     const int gth = group_lanes(l.L);
     if (gth < 32) {
+        // whole warps of lines, as many as let three blocks share an SM's
+        // shared memory (the kernel is built for three resident blocks)
+        const int per_warp = 32 / gth;
         int lpb = 256 / gth;
-        while (lpb > 32 / gth && group_smem(g, l.L, lpb) > 227 * 1024) lpb /= 2;
+        while (lpb > per_warp && 3 * group_smem(g, l.L, lpb) > 227 * 1024) lpb -= per_warp;
         const size_t smem = group_smem(g, l.L, lpb);
         static size_t granted_group[64] = {0};
         int dev = 0;

@@ -31,6 +31,7 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -68,6 +69,11 @@ struct LineTask {
     int32_t out_sel;  // BUF_OUT sinks: 0 y, 1 grad_h, 2 grad_x
 };
 
+// An operand line reads the h buffer when it is read conjugated (the
+// ifft of the generating array), the x buffer otherwise; one launch may hold
+// lines of both.
+__host__ __device__ inline bool reads_h(const LineTask& t) { return t.src_conj != 0; }
+
 struct AlphaTask {
     int32_t nops, idx;
     int64_t count;
@@ -91,7 +97,7 @@ struct Launch {
     int kind;  // 0 line, 1 alpha, 2 accumulate
     int first, count, L;
     int role;  // ROLE_SPECTRUM: spectra, always run; ROLE_PRODUCT: only when y is wanted
-    int what;  // buffers of a run: 0 workspace source, 1 h operand, 2 x operand, 3 + sel output sink
+    int what;  // buffers of a run: 0 workspace source, 1 operands (h and x), 3 + sel output sink
 };
 
 template <typename T>
@@ -151,7 +157,7 @@ constexpr int TWG_SMEM = tw_table_elems(16384);
 // the line the source read.
 template <typename T>
 __global__ void __launch_bounds__(512) line_kernel(const LineTask* __restrict__ tasks, int first,
-                                                   const void* __restrict__ in, void* out, cx<T>* ws,
+                                                   const void* in_h, const void* in_x, void* out, cx<T>* ws,
                                                    const cx<T>* __restrict__ tw_all, int Lmax) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int64_t ops_s[MAXOPS];
@@ -166,6 +172,7 @@ __global__ void __launch_bounds__(512) line_kernel(const LineTask* __restrict__ 
     g.sync();
     if (t.src_mode == SRC_OPERAND) {
         const bool real = t.dst_real & 2;  // bit 1 of dst_real flags a real input operand
+        const void* in = reads_h(t) ? in_h : in_x;
         const void* sbase = (const char*)in + t.src * (real ? sizeof(T) : sizeof(cx<T>));
         const OperandLoad<T> ld{sbase, t.src_len, t.src_stride, t.src_conj, real ? 1 : 0};
         for (int i = g.tid; i < P.L; i += g.nthr) b0[sp(i)] = ld(i);
@@ -188,8 +195,9 @@ __global__ void __launch_bounds__(512) line_kernel(const LineTask* __restrict__ 
 // loads the twiddle table once.  Built for three resident blocks per SM.
 template <typename T>
 __global__ void __launch_bounds__(256, 3) line_group_kernel(const LineTask* __restrict__ tasks, int first, int count,
-                                                         int lpb, int gth, const void* __restrict__ in, void* out,
-                                                         cx<T>* ws, const cx<T>* __restrict__ tw_all, int L) {
+                                                         int lpb, int gth, const void* in_h, const void* in_x,
+                                                         void* out, cx<T>* ws, const cx<T>* __restrict__ tw_all,
+                                                         int L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T>* tws = reinterpret_cast<cx<T>*>(smem_raw + RED_BYTES);
     cx<T>* bufs = tws + TWG_SMEM;
@@ -214,6 +222,7 @@ __global__ void __launch_bounds__(256, 3) line_group_kernel(const LineTask* __re
     cx<T>* b1 = b0 + E;
     if (t.src_mode == SRC_OPERAND) {
         const bool real = t.dst_real & 2;
+        const void* in = reads_h(t) ? in_h : in_x;
         const void* sbase = (const char*)in + t.src * (real ? sizeof(T) : sizeof(cx<T>));
         const OperandLoad<T> ld{sbase, t.src_len, t.src_stride, t.src_conj, real ? 1 : 0};
         for (int i = g.tid; i < L; i += g.nthr) b0[sp(i)] = ld(i);
@@ -527,11 +536,12 @@ int nthr_for(int L) {
     return std::max(32, std::min(512, p));
 }
 
-// Buffers a line task reads and writes: 0 workspace source, 1 h operand,
-// 2 x operand, 3 + sel an output sink (grad_h / grad_x).
+// Buffers a line task reads and writes: 0 workspace source, 1 an operand
+// buffer (h or x: the kernels take both and each line picks its own,
+// reads_h), 3 + sel an output sink (grad_h / grad_x).
 int task_class(const LineTask& t) {
     if (t.dst_buf == BUF_OUT && t.out_sel != 0) return 3 + t.out_sel;
-    if (t.src_mode == SRC_OPERAND) return t.src_conj ? 1 : 2;
+    if (t.src_mode == SRC_OPERAND) return 1;
     return 0;
 }
 
@@ -651,9 +661,27 @@ size_t group_smem(const GeneralPlan* g, int L, int lpb) {
            (size_t)lpb * MAXOPS * sizeof(int64_t);
 }
 
+// Raise a kernel's dynamic shared-memory limit only when a launch needs more
+// than was granted (no attribute calls in steady state, so the launches can
+// be captured into CUDA graphs); grants are kept per device and kernel,
+// under a lock (plans may run on several host threads).
+cudaError_t grant_smem(const void* fn, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> granted;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    size_t& have = granted[std::make_pair(dev, fn)];
+    if (bytes <= have) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) have = bytes;
+    return e;
+}
+
 template <typename T>
-cudaError_t run_lines(GeneralPlan* g, const Launch& l, const LineTask* d_tasks, const void* in, void* out,
-                      cudaStream_t st) {
+cudaError_t run_lines(GeneralPlan* g, const Launch& l, const LineTask* d_tasks, const void* in_h, const void* in_x,
+                      void* out, cudaStream_t st) {
     const int gth = group_lanes(l.L);
     if (gth < 32) {
         // whole warps of lines, as many as let three blocks share an SM's
@@ -662,33 +690,17 @@ cudaError_t run_lines(GeneralPlan* g, const Launch& l, const LineTask* d_tasks, 
         int lpb = 256 / gth;
         while (lpb > per_warp && 3 * group_smem(g, l.L, lpb) > 227 * 1024) lpb -= per_warp;
         const size_t smem = group_smem(g, l.L, lpb);
-        static size_t granted_group[64] = {0};
-        int dev = 0;
-        cudaError_t e = cudaGetDevice(&dev);
+        cudaError_t e = grant_smem(reinterpret_cast<const void*>(line_group_kernel<T>), smem);
         if (e != cudaSuccess) return e;
-        if (smem > granted_group[dev & 63]) {
-            e = cudaFuncSetAttribute(line_group_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            granted_group[dev & 63] = smem;
-        }
         const int blocks = (l.count + lpb - 1) / lpb;
-        line_group_kernel<T><<<blocks, lpb * gth, smem, st>>>(d_tasks, l.first, l.count, lpb, gth, in, out,
+        line_group_kernel<T><<<blocks, lpb * gth, smem, st>>>(d_tasks, l.first, l.count, lpb, gth, in_h, in_x, out,
                                                               (cx<T>*)g->d_ws, (const cx<T>*)g->d_tw, l.L);
         return cudaGetLastError();
     }
     const size_t smem = line_smem(g, l.L);
-    // raise the limit only when needed (no attribute calls in steady state,
-    // so the launches can be captured into CUDA graphs); per device
-    static size_t granted[64] = {0};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    cudaError_t e = grant_smem(reinterpret_cast<const void*>(line_kernel<T>), smem);
     if (e != cudaSuccess) return e;
-    if (smem > granted[dev & 63]) {
-        e = cudaFuncSetAttribute(line_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        granted[dev & 63] = smem;
-    }
-    line_kernel<T><<<l.count, nthr_for(l.L), smem, st>>>(d_tasks, l.first, in, out, (cx<T>*)g->d_ws,
+    line_kernel<T><<<l.count, nthr_for(l.L), smem, st>>>(d_tasks, l.first, in_h, in_x, out, (cx<T>*)g->d_ws,
                                                        (const cx<T>*)g->d_tw, l.L);
     return cudaGetLastError();
 }
@@ -985,9 +997,8 @@ hankel_status general_forward(GeneralPlan* g, const void* h, const void* x, void
     }
     cudaError_t e = run_program(
         g->fwd_prog, [&](const Launch& l) { return l.role == ROLE_PRODUCT && y == nullptr; },
-        [&](const Launch& l, int what) {
-            const void* in = (what == 1) ? h : x;
-            return g->dbl ? run_lines<double>(g, l, g->d_fwd, in, y, st) : run_lines<float>(g, l, g->d_fwd, in, y, st);
+        [&](const Launch& l, int) {
+            return g->dbl ? run_lines<double>(g, l, g->d_fwd, h, x, y, st) : run_lines<float>(g, l, g->d_fwd, h, x, y, st);
         });
     if (e != cudaSuccess) return cuerr(e, "general forward launch", err);
     if (alpha != nullptr) {
@@ -1009,14 +1020,15 @@ hankel_status general_backward(GeneralPlan* g, const void* gy, const void* h, co
         err = "plan has no general program";
         return HANKEL_EINVAL;
     }
-    auto lines = [&](const Launch& l, const void* in, void* out) {
-        return g->dbl ? run_lines<double>(g, l, g->d_bwd, in, out, st) : run_lines<float>(g, l, g->d_bwd, in, out, st);
+    auto lines = [&](const Launch& l, const void* in_h, const void* in_x, void* out) {
+        return g->dbl ? run_lines<double>(g, l, g->d_bwd, in_h, in_x, out, st)
+                      : run_lines<float>(g, l, g->d_bwd, in_h, in_x, out, st);
     };
     cudaError_t e = cudaSuccess;
     if (!(g->flags & HANKEL_STORE_SPECTRA)) {
         e = run_program(
             g->bwd_prog_spec, [](const Launch&) { return false; },
-            [&](const Launch& l, int what) { return lines(l, what == 1 ? h : x, nullptr); });
+            [&](const Launch& l, int) { return lines(l, h, x, nullptr); });
         if (e != cudaSuccess) return cuerr(e, "backward spectra launch", err);
     }
     e = run_program(
@@ -1033,9 +1045,9 @@ hankel_status general_backward(GeneralPlan* g, const void* gy, const void* h, co
             }
             if (what >= 3) {  // gradient stores: grad_h (sel 1) or grad_x (sel 2)
                 void* dst = (what == 4) ? gh : gx;
-                return dst ? lines(l, nullptr, dst) : cudaSuccess;
+                return dst ? lines(l, nullptr, nullptr, dst) : cudaSuccess;
             }
-            return lines(l, gy, nullptr);  // G arrays read grad_y; the rest read workspace
+            return lines(l, gy, gy, nullptr);  // G arrays read grad_y; the rest read workspace
         });
     if (e != cudaSuccess) return cuerr(e, "backward launch", err);
     return HANKEL_OK;

@@ -97,7 +97,7 @@ struct Launch {
     int kind;  // 0 line, 1 alpha, 2 accumulate
     int first, count, L;
     int role;  // ROLE_SPECTRUM: spectra, always run; ROLE_PRODUCT: only when y is wanted
-    int what;  // buffers of a run: 0 workspace source, 1 operands (h and x), 3 + sel output sink
+    int what;  // buffers of a run: 0 workspace source, 1 operands (h and x), 3 gradient sinks
 };
 
 template <typename T>
@@ -150,15 +150,46 @@ struct LineSink {
 // shared-memory slots of the twiddle table (lengths up to 16384)
 constexpr int TWG_SMEM = tw_table_elems(16384);
 
+// The caller's buffers a launch of lines may touch: operand lines read h or
+// x (reads_h), output sinks write y, grad_h or grad_x (out_sel 0, 1, 2); a
+// null sink is a result the caller did not ask for, whose lines store nothing.
+struct LineBufs {
+    const void* in_h;
+    const void* in_x;
+    void* y;
+    void* grad_h;
+    void* grad_x;
+};
+
+// Loader of an operand line (bit 1 of dst_real flags a real input operand).
+template <typename T>
+__device__ __forceinline__ OperandLoad<T> operand_load(const LineTask& t, const LineBufs& b) {
+    const bool real = t.dst_real & 2;
+    const void* in = reads_h(t) ? b.in_h : b.in_x;
+    return OperandLoad<T>{(const char*)in + t.src * (real ? sizeof(T) : sizeof(cx<T>)), t.src_len, t.src_stride,
+                          t.src_conj, real ? 1 : 0};
+}
+
+// Sink of a line: plan workspace, or the caller's buffer that out_sel names
+// (bit 0 of dst_real: real output); a null buffer stores nothing.
+template <typename T>
+__device__ __forceinline__ LineSink<T> line_sink(const LineTask& t, const LineBufs& b, cx<T>* ws) {
+    const int real = t.dst_real & 1;
+    if (t.dst_buf == BUF_WS) return LineSink<T>{ws + t.dst, t.dst_len, t.dst_stride, t.dst_conj, real, (T)t.scale};
+    void* out = (t.out_sel == 0) ? b.y : (t.out_sel == 1) ? b.grad_h : b.grad_x;
+    if (out == nullptr) return LineSink<T>{nullptr, 0, t.dst_stride, t.dst_conj, real, (T)t.scale};
+    return LineSink<T>{(char*)out + t.dst * (real ? sizeof(T) : sizeof(cx<T>)), t.dst_len, t.dst_stride, t.dst_conj,
+                       real, (T)t.scale};
+}
+
 // One line per block: the line's input (an operand line, or a product of
 // spectral arrays) is staged in shared memory, transformed by the stage
 // transform (fft_stage.cuh) and its prefix stored through the sink.  All
 // reads of the line finish before the first store, so a sink may overwrite
 // the line the source read.
 template <typename T>
-__global__ void __launch_bounds__(512) line_kernel(const LineTask* __restrict__ tasks, int first,
-                                                   const void* in_h, const void* in_x, void* out, cx<T>* ws,
-                                                   const cx<T>* __restrict__ tw_all, int Lmax) {
+__global__ void __launch_bounds__(512) line_kernel(const LineTask* __restrict__ tasks, int first, LineBufs io,
+                                                   cx<T>* ws, const cx<T>* __restrict__ tw_all, int Lmax) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int64_t ops_s[MAXOPS];
     cx<T>* tws = reinterpret_cast<cx<T>*>(smem_raw + RED_BYTES);
@@ -171,20 +202,14 @@ __global__ void __launch_bounds__(512) line_kernel(const LineTask* __restrict__ 
     if (g.tid < MAXOPS) ops_s[g.tid] = t.ops[g.tid];
     g.sync();
     if (t.src_mode == SRC_OPERAND) {
-        const bool real = t.dst_real & 2;  // bit 1 of dst_real flags a real input operand
-        const void* in = reads_h(t) ? in_h : in_x;
-        const void* sbase = (const char*)in + t.src * (real ? sizeof(T) : sizeof(cx<T>));
-        const OperandLoad<T> ld{sbase, t.src_len, t.src_stride, t.src_conj, real ? 1 : 0};
+        const OperandLoad<T> ld = operand_load<T>(t, io);
         for (int i = g.tid; i < P.L; i += g.nthr) b0[sp(i)] = ld(i);
     } else {
         const ProductLoad<T> ld{ws, ops_s, t.nops, t.src_len, t.src_conj, t.loff, t.lstride};
         for (int i = g.tid; i < P.L; i += g.nthr) b0[sp(i)] = ld(i);
     }
     g.sync();
-    void* dbase = (t.dst_buf == BUF_WS) ? (void*)(ws + t.dst)
-                                        : (void*)((char*)out + t.dst * ((t.dst_real & 1) ? sizeof(T) : sizeof(cx<T>)));
-    fft_stage<T>(P, GLd<T>{nullptr, 0, nullptr, 0}, b0, b1, b0,
-                 LineSink<T>{dbase, t.dst_len, t.dst_stride, t.dst_conj, t.dst_real & 1, (T)t.scale}, false, tw, g);
+    fft_stage<T>(P, GLd<T>{nullptr, 0, nullptr, 0}, b0, b1, b0, line_sink<T>(t, io, ws), false, tw, g);
 }
 
 // Short lines, several per warp (lines of one launch share their length L):
@@ -195,9 +220,8 @@ __global__ void __launch_bounds__(512) line_kernel(const LineTask* __restrict__ 
 // loads the twiddle table once.  Built for three resident blocks per SM.
 template <typename T>
 __global__ void __launch_bounds__(256, 3) line_group_kernel(const LineTask* __restrict__ tasks, int first, int count,
-                                                         int lpb, int gth, const void* in_h, const void* in_x,
-                                                         void* out, cx<T>* ws, const cx<T>* __restrict__ tw_all,
-                                                         int L) {
+                                                         int lpb, int gth, LineBufs io, cx<T>* ws,
+                                                         const cx<T>* __restrict__ tw_all, int L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T>* tws = reinterpret_cast<cx<T>*>(smem_raw + RED_BYTES);
     cx<T>* bufs = tws + TWG_SMEM;
@@ -221,20 +245,14 @@ __global__ void __launch_bounds__(256, 3) line_group_kernel(const LineTask* __re
     cx<T>* b0 = bufs + (2 * j) * E;
     cx<T>* b1 = b0 + E;
     if (t.src_mode == SRC_OPERAND) {
-        const bool real = t.dst_real & 2;
-        const void* in = reads_h(t) ? in_h : in_x;
-        const void* sbase = (const char*)in + t.src * (real ? sizeof(T) : sizeof(cx<T>));
-        const OperandLoad<T> ld{sbase, t.src_len, t.src_stride, t.src_conj, real ? 1 : 0};
+        const OperandLoad<T> ld = operand_load<T>(t, io);
         for (int i = g.tid; i < L; i += g.nthr) b0[sp(i)] = ld(i);
     } else {
         const ProductLoad<T> ld{ws, ops_all + j * MAXOPS, t.nops, t.src_len, t.src_conj, t.loff, t.lstride};
         for (int i = g.tid; i < L; i += g.nthr) b0[sp(i)] = ld(i);
     }
     g.sync();
-    void* dbase = (t.dst_buf == BUF_WS) ? (void*)(ws + t.dst)
-                                        : (void*)((char*)out + t.dst * ((t.dst_real & 1) ? sizeof(T) : sizeof(cx<T>)));
-    fft_stage<T>(t.P, GLd<T>{nullptr, 0, nullptr, 0}, b0, b1, b0,
-                 LineSink<T>{dbase, t.dst_len, t.dst_stride, t.dst_conj, t.dst_real & 1, (T)t.scale}, false, tw, g);
+    fft_stage<T>(t.P, GLd<T>{nullptr, 0, nullptr, 0}, b0, b1, b0, line_sink<T>(t, io, ws), false, tw, g);
 }
 
 template <typename T>
@@ -537,10 +555,11 @@ int nthr_for(int L) {
 }
 
 // Buffers a line task reads and writes: 0 workspace source, 1 an operand
-// buffer (h or x: the kernels take both and each line picks its own,
-// reads_h), 3 + sel an output sink (grad_h / grad_x).
+// buffer (h or x), 3 a gradient sink (grad_h or grad_x).  The kernels take
+// every buffer and each line picks its own (LineBufs), so these classes only
+// order the launches of a phase.
 int task_class(const LineTask& t) {
-    if (t.dst_buf == BUF_OUT && t.out_sel != 0) return 3 + t.out_sel;
+    if (t.dst_buf == BUF_OUT && t.out_sel != 0) return 3;
     if (t.src_mode == SRC_OPERAND) return 1;
     return 0;
 }
@@ -680,8 +699,8 @@ cudaError_t grant_smem(const void* fn, size_t bytes) {
 }
 
 template <typename T>
-cudaError_t run_lines(GeneralPlan* g, const Launch& l, const LineTask* d_tasks, const void* in_h, const void* in_x,
-                      void* out, cudaStream_t st) {
+cudaError_t run_lines(GeneralPlan* g, const Launch& l, const LineTask* d_tasks, const LineBufs& io,
+                      cudaStream_t st) {
     const int gth = group_lanes(l.L);
     if (gth < 32) {
         // whole warps of lines, as many as let three blocks share an SM's
@@ -693,14 +712,14 @@ cudaError_t run_lines(GeneralPlan* g, const Launch& l, const LineTask* d_tasks, 
         cudaError_t e = grant_smem(reinterpret_cast<const void*>(line_group_kernel<T>), smem);
         if (e != cudaSuccess) return e;
         const int blocks = (l.count + lpb - 1) / lpb;
-        line_group_kernel<T><<<blocks, lpb * gth, smem, st>>>(d_tasks, l.first, l.count, lpb, gth, in_h, in_x, out,
+        line_group_kernel<T><<<blocks, lpb * gth, smem, st>>>(d_tasks, l.first, l.count, lpb, gth, io,
                                                               (cx<T>*)g->d_ws, (const cx<T>*)g->d_tw, l.L);
         return cudaGetLastError();
     }
     const size_t smem = line_smem(g, l.L);
     cudaError_t e = grant_smem(reinterpret_cast<const void*>(line_kernel<T>), smem);
     if (e != cudaSuccess) return e;
-    line_kernel<T><<<l.count, nthr_for(l.L), smem, st>>>(d_tasks, l.first, in_h, in_x, out, (cx<T>*)g->d_ws,
+    line_kernel<T><<<l.count, nthr_for(l.L), smem, st>>>(d_tasks, l.first, io, (cx<T>*)g->d_ws,
                                                        (const cx<T>*)g->d_tw, l.L);
     return cudaGetLastError();
 }
@@ -998,7 +1017,8 @@ hankel_status general_forward(GeneralPlan* g, const void* h, const void* x, void
     cudaError_t e = run_program(
         g->fwd_prog, [&](const Launch& l) { return l.role == ROLE_PRODUCT && y == nullptr; },
         [&](const Launch& l, int) {
-            return g->dbl ? run_lines<double>(g, l, g->d_fwd, h, x, y, st) : run_lines<float>(g, l, g->d_fwd, h, x, y, st);
+            const LineBufs io{h, x, y, nullptr, nullptr};
+            return g->dbl ? run_lines<double>(g, l, g->d_fwd, io, st) : run_lines<float>(g, l, g->d_fwd, io, st);
         });
     if (e != cudaSuccess) return cuerr(e, "general forward launch", err);
     if (alpha != nullptr) {
@@ -1020,15 +1040,14 @@ hankel_status general_backward(GeneralPlan* g, const void* gy, const void* h, co
         err = "plan has no general program";
         return HANKEL_EINVAL;
     }
-    auto lines = [&](const Launch& l, const void* in_h, const void* in_x, void* out) {
-        return g->dbl ? run_lines<double>(g, l, g->d_bwd, in_h, in_x, out, st)
-                      : run_lines<float>(g, l, g->d_bwd, in_h, in_x, out, st);
+    auto lines = [&](const Launch& l, const LineBufs& io) {
+        return g->dbl ? run_lines<double>(g, l, g->d_bwd, io, st) : run_lines<float>(g, l, g->d_bwd, io, st);
     };
     cudaError_t e = cudaSuccess;
     if (!(g->flags & HANKEL_STORE_SPECTRA)) {
         e = run_program(
             g->bwd_prog_spec, [](const Launch&) { return false; },
-            [&](const Launch& l, int) { return lines(l, h, x, nullptr); });
+            [&](const Launch& l, int) { return lines(l, LineBufs{h, x, nullptr, nullptr, nullptr}); });
         if (e != cudaSuccess) return cuerr(e, "backward spectra launch", err);
     }
     e = run_program(
@@ -1043,11 +1062,10 @@ hankel_status general_backward(GeneralPlan* g, const void* gy, const void* h, co
                                                                             (cx<float>*)g->d_ws);
                 return cudaGetLastError();
             }
-            if (what >= 3) {  // gradient stores: grad_h (sel 1) or grad_x (sel 2)
-                void* dst = (what == 4) ? gh : gx;
-                return dst ? lines(l, nullptr, nullptr, dst) : cudaSuccess;
-            }
-            return lines(l, gy, gy, nullptr);  // G arrays read grad_y; the rest read workspace
+            if (what == 3 && gh == nullptr && gx == nullptr) return cudaSuccess;  // no gradient wanted
+            // G arrays read grad_y, the rest read workspace; gradient lines store
+            // into grad_h (sel 1) or grad_x (sel 2) when the caller passed it
+            return lines(l, LineBufs{gy, gy, nullptr, gh, gx});
         });
     if (e != cudaSuccess) return cuerr(e, "backward launch", err);
     return HANKEL_OK;

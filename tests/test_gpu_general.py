@@ -261,3 +261,47 @@ def test_block_backward_shared_generator(dev, share_H):
         got = gh[:d1 * d2].reshape(d2, d1).T
         assert rel(got, total) <= 1e-11
     plan.close()
+
+
+@pytest.mark.parametrize("block", [False, True])
+def test_backward_one_gradient_only(dev, block):
+    """An adjoint call that asks for grad_h alone, or grad_x alone, gives the
+    same values as the call that asks for both (the gradient lines of both
+    kinds share launches; a line whose buffer is absent stores nothing)."""
+    rng = np.random.default_rng(21)
+    if block:
+        n, N = [3, 4, 3], [4, 2, 3]
+        Hs, Xs_all, descs, pk = block_case(n, N, True, rng, count=3, share_H=False)
+        G = np.concatenate([rnd(rng, (n[0], N[0]), True).reshape(-1, order="F") for _ in range(3)])
+        flags = hk.BLOCK
+    else:
+        cases = [[5, 3, 4], [40, 9, 30], [7, 7]]
+        pk = Packer(True)
+        descs = hk.make_descs(len(cases))
+        yoff = 0
+        for i, dims in enumerate(cases):
+            m = len(dims)
+            descs[i]["m"] = m
+            descs[i]["n"][:m] = dims
+            descs[i]["h_off"] = pk.add_h(rnd(rng, oracle.d_of(dims), True))
+            for p in range(m):
+                descs[i]["x_off"][p] = pk.add_x(rnd(rng, dims[p], True))
+            descs[i]["y_off"] = yoff
+            yoff += dims[0]
+        G = rnd(rng, yoff, True)
+        flags = 0
+    H, X = pk.arrays()
+    plan = hk.Plan(descs, hk.C128, flags)
+    args = (to_dev(G, hk.C128, dev), to_dev(H, hk.C128, dev), to_dev(X, hk.C128, dev))
+    both_h = torch.zeros(H.size, dtype=torch.complex128, device=dev)
+    both_x = torch.zeros(X.size, dtype=torch.complex128, device=dev)
+    plan.backward(*args, both_h, both_x)
+    only_h = torch.zeros_like(both_h)
+    plan.backward(*args, only_h, None)
+    only_x = torch.zeros_like(both_x)
+    plan.backward(*args, None, only_x)
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(both_h).item() > 0 and torch.count_nonzero(both_x).item() > 0
+    assert torch.equal(only_h, both_h)
+    assert torch.equal(only_x, both_x)
+    plan.close()

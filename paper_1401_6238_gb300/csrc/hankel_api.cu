@@ -1086,10 +1086,19 @@ hankel_status hankel_txv_host(hankel_plan_t p, const void* h, const void* x, voi
     const size_t ab = (size_t)p->descs.size() * es;
     cudaError_t e;
     if (!p->s_h) {
-        if ((e = cudaMalloc(&p->s_h, hb)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(staging)");
-        if ((e = cudaMalloc(&p->s_x, xb)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(staging)");
-        if ((e = cudaMalloc(&p->s_y, yb)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(staging)");
-        if ((e = cudaMalloc(&p->s_a, ab)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(staging)");
+        // all four staging buffers or none (a failed call leaves the plan as it was)
+        void* sb[4] = {nullptr, nullptr, nullptr, nullptr};
+        const size_t bytes[4] = {hb, xb, yb, ab};
+        for (int i = 0; i < 4; ++i) {
+            if ((e = cudaMalloc(&sb[i], bytes[i])) != cudaSuccess) {
+                for (int j = 0; j < i; ++j) cudaFree(sb[j]);
+                return cuda_fail(e, "cudaMalloc(staging)");
+            }
+        }
+        p->s_h = sb[0];
+        p->s_x = sb[1];
+        p->s_y = sb[2];
+        p->s_a = sb[3];
     }
     cudaStream_t st = (cudaStream_t)stream;
     // Large batches run as a pipeline of contiguous descriptor ranges: the

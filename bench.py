@@ -125,7 +125,8 @@ def read_clocks(path, proc, gpu_index):
     if not sm:
         return None
     return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
-            "samples": len(sm)}
+            "samples": len(sm), "window": "%.1f s soak of the same step just before the timed region, and the "
+                                          "timed region" % SOAK_SECONDS}
 
 
 def rank_seed(rank):
@@ -166,6 +167,8 @@ def profiled_traffic():
 
 
 FP32_LANES_PER_SM, SMS = 128, 152
+# untimed run of the step under the clock sampler before the timed region
+SOAK_SECONDS = 0.8
 
 
 def alu_roofline(flops, kernel_ms, clocks):
@@ -499,13 +502,22 @@ def main():
     for i in range(args.warmup):
         step(i)
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    # per-run clock samples; BENCH_CLOCKS_CSV keeps them at a chosen path
+    # per-run clock samples; BENCH_CLOCKS_CSV keeps them at a chosen path.
+    # nvidia-smi samples every 200 ms and the timed steps last milliseconds,
+    # so the samples cover a soak of the same step run on every rank right
+    # before the timed region, and the timed region itself
     clk_path = os.environ.get("BENCH_CLOCKS_CSV") or os.path.join(
         tempfile.gettempdir(), "bench_clocks_%d.csv" % os.getpid())
     sampler = start_clock_sampler(clk_path) if rank == 0 else None
-    time.sleep(0.3 if sampler else 0)
+    soak_end = time.perf_counter() + SOAK_SECONDS
+    i = args.warmup
+    while time.perf_counter() < soak_end:
+        for _ in range(25):
+            step(i)
+            i += 1
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     t_start = torch.cuda.Event(enable_timing=True)

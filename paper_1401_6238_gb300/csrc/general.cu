@@ -261,15 +261,14 @@ __global__ void __launch_bounds__(256) alpha_kernel(const AlphaTask* __restrict_
     __shared__ double red[64];
     const AlphaTask& t = tasks[first + blockIdx.x];
     const Group g{(int)threadIdx.x, (int)blockDim.x, 0};
+    // products in T precision, their sum in FP64 (FP64 arithmetic is slow on
+    // this part: one conversion and one FP64 add per element and component)
     double sr = 0.0, si = 0.0;
     for (int64_t e = g.tid; e < t.count; e += g.nthr) {
-        cx<double> v = mk<double>(1.0, 0.0);
-        for (int q = 0; q < t.nops; ++q) {
-            const cx<T> w = ws[t.ops[q] + e];
-            v = cmul(v, mk<double>((double)w.x, (double)w.y));
-        }
-        sr += v.x;
-        si += v.y;
+        cx<T> v = ws[t.ops[0] + e];
+        for (int q = 1; q < t.nops; ++q) v = cmul(v, ws[t.ops[q] + e]);
+        sr += (double)v.x;
+        si += (double)v.y;
     }
     sr = group_sum(sr, red, g);
     si = group_sum(si, red, g);

@@ -296,15 +296,20 @@ __global__ void __launch_bounds__(512) real_multi_kernel(const MultiJob* __restr
             const int kc = (k == 0) ? 0 : L - k;
             cx<T> XA, XB;
             unpack(S[sp(k)], conjg(S[sp(kc)]), XA, XB);
+            // terms in T precision, summed in FP64 (one conversion and one
+            // FP64 add per term: FP64 arithmetic is slow on this part)
+            T tA, tB;
             if (kc == k) {
                 const cx<T> v = acc[sp(k)];
-                aA += (double)v.x * (double)XA.x;
-                aB += (double)v.y * (double)XB.x;
+                tA = v.x * XA.x;
+                tB = v.y * XB.x;
             } else {
                 const cx<T> PA = acc[sp(k)], PB = acc[sp(kc)];
-                aA += 2.0 * ((double)PA.x * XA.x - (double)PA.y * XA.y);
-                aB += 2.0 * ((double)PB.x * XB.x - (double)PB.y * XB.y);
+                tA = T(2) * (PA.x * XA.x - PA.y * XA.y);
+                tB = T(2) * (PB.x * XB.x - PB.y * XB.y);
             }
+            aA += (double)tA;
+            aB += (double)tB;
         }
         const double sA = group_sum(aA, red, g);
         const double sB = two ? group_sum(aB, red, g) : 0.0;

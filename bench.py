@@ -221,6 +221,30 @@ def sec_grad(dev, stream, steps, warmup):
     return out
 
 
+def sec_batch_adjoint(dev, stream, steps, warmup):
+    import torch
+    from paper_1401_6238_gb300 import hankel as hk
+    from paper_1401_6238_gb300 import workloads as wl
+    out = {}
+    # adjoint of the benchmark batch: grad_h and grad_x of <g, y> for the
+    # 8192 tensors (spectra recomputed, not kept from a forward call)
+    b = wl.batched_square(count=8192, seed=1)
+    plan = hk.Plan(hk.batch_descs(b), hk.R32, hk.SAME_X)
+    H = torch.tensor(b.h, dtype=torch.float32, device=dev)
+    X = torch.tensor(b.x, dtype=torch.float32, device=dev)
+    G = torch.tensor(np.random.default_rng(0).standard_normal(b.y_len), dtype=torch.float32, device=dev)
+    gh, gx = torch.zeros_like(H), torch.zeros_like(X)
+    ms = timed(lambda: plan.backward(G, H, X, gh, gx, stream), steps, warmup, stream)
+    # read g, h, x and write grad_h, grad_x: 4 (2 d + 3 n) bytes per tensor
+    alg = float(sum(4 * (2 * (m * (n - 1) + 1) + 3 * n) for m, n in zip(b.orders, b.dims)))
+    out["batch_adjoint"] = {"workload": "adjoint of the 8192-tensor batch (grad_h, grad_x of <g, y>), FP32, spectra "
+                                        "recomputed", "value": len(b) / (ms / 1e3), "unit": "adjoint products/s",
+                            "ms_per_step": ms, "algorithmic_bytes": alg,
+                            "achieved_gbs": alg / (ms / 1e3) / 1e9, "launches": plan.info["launches"]}
+    plan.close()
+    return out
+
+
 def sec_hooi_products(dev, stream, steps, warmup):
     import torch
     from paper_1401_6238_gb300 import hankel as hk
@@ -351,7 +375,8 @@ def sec_level3(dev, stream, steps, warmup):
     return out
 
 
-SECONDARY = {"grad": sec_grad, "hooi_products": sec_hooi_products, "bhhb": sec_bhhb, "distinct": sec_distinct,
+SECONDARY = {"grad": sec_grad, "batch_adjoint": sec_batch_adjoint, "hooi_products": sec_hooi_products,
+             "bhhb": sec_bhhb, "distinct": sec_distinct,
              "level3": sec_level3}
 
 
@@ -449,8 +474,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-secondary", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--secondary", default=None,
-                    help="comma-separated secondary workloads to run alone (grad, hooi_products, bhhb, distinct, "
-                         "level3, edf); prints their JSON and exits")
+                    help="comma-separated secondary workloads to run alone (grad, batch_adjoint, hooi_products, bhhb, "
+                         "distinct, level3, edf); prints their JSON and exits")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -473,13 +473,26 @@ hankel_status build_real_path(hankel_plan_s* p) {
         }
         p->fwd_jobs.push_back(J);
     }
-    for (int64_t i = 0; i < count; ++i) {
+    // adjoint: tensors of one length in pairs that share the transform of
+    // their upstream gradients (three shared buffers), longer ones alone
+    const bool pair_bwd = (p->flags & HANKEL_ONE_PER_LAUNCH) == 0;
+    for (size_t k = 0; k < order.size();) {
         hk::RealJob J;
         std::memset(&J, 0, sizeof(J));
-        J.P = fft_plan_of(p, p->Lof[i]);
-        fill(J, i, false);
-        J.single = 1;
+        const int64_t a = order[k];
+        const int L = p->Lof[a];
+        J.P = fft_plan_of(p, L);
+        fill(J, a, false);
         J.iB = -1;
+        J.single = 1;
+        k += 1;
+        if (pair_bwd && L <= max_pair_L) {
+            J.single = 0;
+            if (k < order.size() && p->Lof[order[k]] == L) {
+                fill(J, order[k], true);
+                k += 1;
+            }
+        }
         p->bwd_jobs.push_back(J);
     }
     // single jobs too long for one block's shared memory run as split jobs

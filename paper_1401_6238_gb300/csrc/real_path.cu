@@ -367,6 +367,64 @@ __global__ void __launch_bounds__(512) real_bwd_kernel(const RealJob* __restrict
     fft_stage<T>(P, GLd<T>{nullptr, 0, nullptr, 0}, F, G, F, store, false, tw, g);
 }
 
+// Pair jobs of the adjoint: tensors A and B with one FFT length share the
+// transform of their upstream gradients, G = fft(g~_A + i g~_B), unpacked per
+// bin (G_A = (G_k + conj G_{L-k})/2, G_B = -i (G_k - conj G_{L-k})/2); U_A
+// and U_B = fft(h~ + i x~) go to (or come from) workspace as in the single
+// job, and each tensor's Q then takes one transform: five transforms per pair
+// instead of six.  G stays in buffer bC while A's and B's transforms use bA
+// and bB.  iB < 0: tensor A alone.
+template <typename T>
+__global__ void __launch_bounds__(512) real_bwd_pair_kernel(const RealJob* __restrict__ jobs, int first,
+                                                             const T* __restrict__ gy, const T* __restrict__ h,
+                                                             const T* __restrict__ x, T* __restrict__ gh,
+                                                             T* __restrict__ gx, const cx<T>* __restrict__ tw_all,
+                                                             cx<T>* ws, int Lmax, int flags, int stored) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T>* tws = reinterpret_cast<cx<T>*>(smem_raw + RED_BYTES);
+    cx<T>* bA = tws + TW_SMEM;
+    cx<T>* bB = bA + smem_elems(Lmax);
+    cx<T>* bC = bB + smem_elems(Lmax);
+    const RealJob J = jobs[first + blockIdx.x];
+    const Group g{(int)threadIdx.x, (int)blockDim.x, 0};
+    const FftPlan P = J.P;
+    const int L = P.L;
+    const TwTab<T> tw = load_twiddles(tws, tw_all + P.tw_off, L, g);
+    g.sync();
+    const bool two = J.iB >= 0;
+    const bool fp64 = (flags & HANKEL_FP64_POWER) != 0;
+    const T invL = T(1) / T(L);
+    cx<T>* UA = ws + J.wsA;
+    cx<T>* UB = ws + J.wsB;
+    const GLd<T> none{nullptr, 0, nullptr, 0};
+    const AdjSt<T> stA{gh ? gh + J.hA : nullptr, J.dA, gx ? gx + J.xA : nullptr, J.nA, L};
+    const AdjSt<T> stB{gh && two ? gh + J.hB : nullptr, J.dB, gx && two ? gx + J.xB : nullptr, J.nB, L};
+    // U_A, U_B = fft(h~ + i x~) straight to workspace (or kept from the forward call)
+    if (!stored) {
+        fft_stage<T>(P, GLd<T>{h + J.hA, J.dA, x + J.xA, J.nA}, nullptr, bA, bB, GSt<T>{UA}, false, tw, g);
+        if (two) fft_stage<T>(P, GLd<T>{h + J.hB, J.dB, x + J.xB, J.nB}, nullptr, bA, bB, GSt<T>{UB}, false, tw, g);
+    }
+    // G = fft(g~_A + i g~_B), ping-ponged so that it ends in bC (the last of
+    // npass passes writes the first buffer when npass is odd): both tensors'
+    // transforms then have bA and bB
+    fft_stage<T>(P, GLd<T>{gy + J.yA, J.nA, two ? gy + J.yB : nullptr, two ? J.nB : 0}, nullptr,
+                 (P.npass & 1) ? bC : bA, (P.npass & 1) ? bA : bC, stA, true, tw, g);
+    for (int t = 0; t < (two ? 2 : 1); ++t) {
+        const cx<T>* U = (t == 0) ? UA : UB;
+        const int m = (t == 0) ? J.mA : J.mB;
+        for (int k = g.tid; k < L; k += g.nthr) {
+            const int kc = (k == 0) ? 0 : L - k;
+            const cx<T> Gk = bC[sp(k)], Gc = conjg(bC[sp(kc)]);
+            // G_A = (G_k + conj G_{L-k}) / 2, G_B = -i (G_k - conj G_{L-k}) / 2
+            const cx<T> Gt = (t == 0) ? scal(Gk + Gc, T(0.5)) : scal(mul_ni(Gk - Gc), T(0.5));
+            const cx<T> Uk = U[k], Uc = conjg(U[kc]);
+            bA[sp(k)] = fp64 ? adjoint_bin<double>(Uk, Uc, Gt, m, invL) : adjoint_bin<T>(Uk, Uc, Gt, m, invL);
+        }
+        g.sync();
+        fft_stage<T>(P, none, bA, bB, bA, (t == 0) ? stA : stB, false, tw, g);
+    }
+}
+
 // Single jobs whose transforms exceed shared memory: the same steps with
 // the transform scratch in global workspace (two L-buffers per job at wsB,
 // L2-resident in practice); shared memory holds only the twiddle table.
@@ -814,6 +872,14 @@ static cudaError_t launch_bwd_t(const RealLaunch& lc, const RealJob* jobs, const
         return cudaGetLastError();
     }
     const size_t smem = real_smem_bytes<T>(lc);
+    if (lc.arrays == 3) {  // pair jobs
+        auto k = real_bwd_pair_kernel<T>;
+        cudaError_t e = ensure_smem(k, smem);
+        if (e != cudaSuccess) return e;
+        k<<<lc.count, lc.nthr, smem, st>>>(jobs, lc.first, (const T*)gy, (const T*)h, (const T*)x, (T*)gh, (T*)gx,
+                                           (const cx<T>*)tw, (cx<T>*)ws, lc.Lmax, flags, stored);
+        return cudaGetLastError();
+    }
     if (lc.arrays == 0) {
         real_bwd_global_kernel<T><<<lc.count, lc.nthr, smem, st>>>(jobs, lc.first, (const T*)gy, (const T*)h,
                                                                    (const T*)x, (T*)gh, (T*)gx, (const cx<T>*)tw,

@@ -99,3 +99,32 @@ def test_store_spectra_equals_recompute(dev):
     c = grads(b, hk.R32, hk.SAME_X | hk.STORE_SPECTRA, g, dev, forward_first=True)
     np.testing.assert_array_equal(a[0], c[0])
     np.testing.assert_array_equal(a[1], c[1])
+
+
+@pytest.mark.parametrize("dtype,tol", [(hk.R32, 2e-5), (hk.R64, 1e-11)])
+@pytest.mark.parametrize("flags", [hk.SAME_X, hk.SAME_X | hk.STORE_SPECTRA])
+def test_backward_pairs_of_one_length(dev, dtype, tol, flags):
+    """Tensors that share an FFT length run the adjoint in pairs (their
+    upstream gradients share one transform): equal sizes, different orders
+    with the same generating length (m=3, n=101 and m=4, n=76: d = 301), and
+    an odd tensor out; every gradient against the oracle."""
+    rng = np.random.default_rng(17)
+    shapes = [(3, 101), (4, 76), (3, 101), (5, 40), (5, 40), (4, 76), (3, 300), (3, 300), (4, 300)]
+    orders, dims, hs, xs = [], [], [], []
+    for m, n in shapes:
+        d = m * (n - 1) + 1
+        orders.append(m)
+        dims.append(n)
+        hs.append(rng.standard_normal(d) / np.sqrt(d))
+        x = rng.standard_normal(n)
+        xs.append(x / np.linalg.norm(x))
+    b = wl.pack_square(orders, dims, hs, xs)
+    g = rng.standard_normal(b.y_len)
+    gh, gx = grads(b, dtype, flags, g, dev, forward_first=bool(flags & hk.STORE_SPECTRA))
+    for i in range(len(b)):
+        m, n, h, x = b.tensor(i)
+        d = len(h)
+        rh, rx = ref_grads(b, g, i)
+        eh = np.max(np.abs(gh[b.h_off[i]: b.h_off[i] + d] - rh)) / np.max(np.abs(rh))
+        ex = np.max(np.abs(gx[b.x_off[i]: b.x_off[i] + n] - rx)) / np.max(np.abs(rx))
+        assert eh <= tol and ex <= tol, (i, m, n, eh, ex)

@@ -575,7 +575,7 @@ def main():
 
     # the same step replayed from a CUDA graph (the launches and the plan's
     # stream fork/join captured once)
-    graph = None
+    graph, local_gms = None, float("inf")  # inf: this rank has no replay time
     try:
         gs = torch.cuda.Stream()
         gs.wait_stream(stream)
@@ -592,12 +592,18 @@ def main():
             cg.replay()
         gb.record(stream)
         torch.cuda.synchronize()
-        gms = max_over_ranks(ga.elapsed_time(gb) / args.steps, dist, dev)
-        graph = {"value": aggregate_rate(world, len(batch), gms / 1000.0), "unit": "products/s",
-                 "ms_per_step": gms, "note": "replays of one captured step on one input copy (L2-warm)"}
+        local_gms = ga.elapsed_time(gb) / args.steps
         del cg
     except Exception as exc:  # report, do not fail the benchmark
         graph = {"error": str(exc)[:200]}
+    # every rank takes part in the max, whether or not its capture worked
+    gms = max_over_ranks(local_gms, dist, dev)
+    if graph is None:
+        if gms != float("inf"):  # every rank timed its replays
+            graph = {"value": aggregate_rate(world, len(batch), gms / 1000.0), "unit": "products/s",
+                     "ms_per_step": gms, "note": "replays of one captured step on one input copy (L2-warm)"}
+        else:
+            graph = {"error": "graph replay failed on another rank"}
 
     # end to end through the host-buffer entry point
     hh = torch.tensor(batch.h, dtype=torch.float32).pin_memory()

@@ -20,6 +20,8 @@ LIB = os.path.join(PKG, "libhankel.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"),
           "-I" + CSRC]
+# extra nvcc flags (e.g. -D defines of tuning constants) from the environment
+CFLAGS += os.environ.get("HANKEL_NVCC_FLAGS", "").split()
 
 
 def nvcc():
@@ -43,6 +45,7 @@ def _stale(obj, deps):
 
 
 def build(verbose=False, force=False):
+    """Compile the .cu files that changed (all with force=True) and link the library."""
     os.makedirs(OUT, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(ROOT, "include", "hankel.h"))

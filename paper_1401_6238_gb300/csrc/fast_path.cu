@@ -1,0 +1,560 @@
+// fast_path.cu -- one persistent launch for batches of real square tensors
+// with one vector per tensor: y = H x^{m-1} and alpha = H x^m (Section 2.1
+// notation), by the embedding of Section 3 at FFT lengths L = R 2T with
+// R in {16, 12} (powers of two and three times powers of two, 32..4096).
+//
+// Work unit: a pair job, two tensors A and B with one FFT length L, run by a
+// group of T = L / (2R) threads.  Per tensor the generating vector and the
+// vector share one complex transform, S = fft(h~ + i x~) (zero-padded on
+// load); bins k and L-k of S give
+//     H_k = (S_k + conj S_{L-k}) / 2,  X_k = -i (S_k - conj S_{L-k}) / 2,
+// the Section 3 spectral product P_k = ifft(h~)_k X_k^{m-1} with
+// ifft(h~)_k = conj(H_k) / L, and alpha = sum_k ifft(h~)_k X_k^m.  P_A and
+// P_B are Hermitian, so y~ = fft(P_A + i P_B) returns y_A in its real part
+// and y_B in its imaginary part (truncated to n on store).  Three length-L
+// transforms per two tensors.
+//
+// Transforms are Stockham passes (fft_core.cuh conventions): pass radix R,
+// Ns = product of the earlier radices, butterfly b takes inputs b + r L/R,
+// multiplies input r by w_{Ns R}^{r (b mod Ns)}, and writes output r to
+// (b - b mod Ns) R + b mod Ns + r Ns.  Forward passes: the power-of-two part
+// of L first, radix R last; the final transform of the product starts with
+// radix R.
+//
+// Register-resident mirror pass.  In the last pass (Ns = L/R, NB = L/R
+// butterflies) thread u of a group holds butterflies u and NB - u (u >= 1),
+// or 0 and NB/2 (u = 0).  Their bins are mirror images: bin u + s NB pairs
+// with bin (NB - u) + (R-1-s) NB, so the unpacking, the spectrum power and
+// the packing of P_A + i P_B need no data from other threads, and the first
+// pass of the final transform (radix R, the same butterflies, no twiddles)
+// starts from these registers.  Butterfly NB - u needs twiddles
+// w_L^{r (NB-u)} = w_R^r conj(w_L^{r u}): the conjugates of its partner's,
+// with the w_R^r factor done as a rotation of the transform's outputs
+// (DFT_R(a_r w_R^r)[s] = DFT_R(a)[s+1]).
+//
+// All other passes go through two shared-memory buffers written alternately
+// (one barrier per pass).  Twiddles come from two FP32 tables rounded from
+// FP64 (w_4096^e and w_3072^e) read through the L1 cache.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "fft_core.cuh"
+#include "launch.h"
+
+namespace hk {
+namespace fp {
+
+#ifndef HK_FAST_MIN_BLOCKS
+#define HK_FAST_MIN_BLOCKS 2  // resident blocks per SM the register budget is sized for
+#endif
+constexpr int BLOCK = 256;                  // threads per block
+constexpr int PTS = 4096;                   // complex points a block's groups hold together
+constexpr int BUF = PTS + PTS / 16;         // padded elements of one exchange buffer
+constexpr int RED = 8;                      // doubles of reduction scratch
+constexpr int STASH = 16;                   // complex slots per thread of the thread-private slab
+// two-level twiddle tables in shared memory: w_4096^e = A2[e >> 6] B2[e & 63],
+// w_3072^e = A3[e >> 6] B3[e & 63] (the stage_twiddle_kernel layout: A then B)
+constexpr int TW2 = 4096 / 64 + 64;
+constexpr int TW3 = 3072 / 64 + 64;
+
+// padded shared-memory index: one slot every 16 elements (bank spread)
+__device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
+
+__host__ __device__ constexpr bool pow2(int v) { return (v & (v - 1)) == 0; }
+// radix of the last pass; the thread group of a job has one thread per
+// last-pass butterfly
+__host__ __device__ constexpr int rlast(int L) { return pow2(L) ? 16 : 12; }
+__host__ __device__ constexpr int nthr(int L) { return L / rlast(L); }
+// radix of the power-of-two passes for Q = L / R: 16 first, then the rest
+__host__ __device__ constexpr int q0(int Q) { return Q >= 16 ? 16 : Q; }
+__host__ __device__ constexpr int q1(int Q) { return Q > 16 ? Q / 16 : 1; }
+
+// Dynamic shared memory of the kernel: reduction scratch, the two-level
+// twiddle tables, the two exchange buffers (fixed offsets, so device
+// functions address it without pointers in registers).
+extern __shared__ __align__(16) unsigned char fp_smem[];
+__device__ __forceinline__ double* sm_red() { return reinterpret_cast<double*>(fp_smem); }
+__device__ __forceinline__ cx<float>* sm_t2() { return reinterpret_cast<cx<float>*>(fp_smem + RED * sizeof(double)); }
+__device__ __forceinline__ cx<float>* sm_t3() { return sm_t2() + TW2; }
+__device__ __forceinline__ cx<float>* sm_buf(int i) { return sm_t3() + TW3 + i * BUF; }
+// thread-private slab: slot s of thread i at sm_stash()[s * BLOCK + i]
+__device__ __forceinline__ cx<float>* sm_stash() { return sm_buf(2); }
+
+struct Tw {
+    // w_M^e for M dividing 4096 (a power of two) or 3072
+    template <int M>
+    __device__ __forceinline__ cx<float> get(int e) const {
+        if constexpr (pow2(M)) {
+            const int f = e * (4096 / M);
+            return cmul(sm_t2()[f >> 6], sm_t2()[64 + (f & 63)]);
+        } else {
+            const int f = e * (3072 / M);
+            return cmul(sm_t3()[f >> 6], sm_t3()[48 + (f & 63)]);
+        }
+    }
+};
+
+template <int R>
+__device__ __forceinline__ void dft(cx<float>* a) { DFT<float, R>::run(a); }
+
+// p[r] = w^r for r = 1 .. R-1 by a multiplication tree of depth <= 4
+// (w^2 = w w, w^4 = w^2 w^2, w^8 = w^4 w^4; any other power one product of
+// those), so each power carries at most four roundings.
+template <int R>
+__device__ __forceinline__ void powers(cx<float> w, cx<float>* p) {
+    p[1] = w;
+    if (R > 2) p[2] = cmul(w, w);
+#pragma unroll
+    for (int r = 3; r < R; ++r) {
+        const int hi = (r >= 8) ? 8 : (r >= 4) ? 4 : 2;
+        p[r] = (r == hi) ? cmul(p[hi / 2], p[hi / 2]) : cmul(p[hi], p[r - hi]);
+    }
+}
+
+// x + i y for complex x, y
+__device__ __forceinline__ cx<float> plus_i(cx<float> a, cx<float> b) { return mk<float>(a.x - b.y, a.y + b.x); }
+__device__ __forceinline__ cx<float> sel(bool c, cx<float> a, cx<float> b) { return c ? a : b; }
+
+// -------------------------------------------------------------- pass pieces
+
+// Asynchronous zero-padded copy of h~ + i x~ (length L, natural order) into
+// a padded buffer: 4-byte cp.async copies whose source size 0 zero-fills
+// (the source address then stays a valid one, the array's start).
+// Completion: stage_wait() and a barrier.
+template <int L, int T>
+__device__ __forceinline__ void stage(cx<float>* buf, const float* h, int d, const float* x, int n, int t) {
+#pragma unroll 4
+    for (int i = t; i < L; i += T) {
+        float* dst = reinterpret_cast<float*>(buf + pad(i));
+        const unsigned da = (unsigned)__cvta_generic_to_shared(dst);
+        const int sa = i < d ? 4 : 0, sb = i < n ? 4 : 0;
+        const float* pa = i < d ? h + i : h;
+        const float* pb = i < n ? x + i : x;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(da), "l"(pa), "r"(sa) : "memory");
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(da + 4), "l"(pb), "r"(sb) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void stage_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// R elements b + r S (r < R) of a padded buffer; when S is a multiple of 16
+// the padded index is linear in r.
+template <int R, int S>
+__device__ __forceinline__ void sload(cx<float>* v, const cx<float>* buf, int b) {
+    if constexpr (S % 16 == 0) {
+        const cx<float>* p = buf + pad(b);
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = p[r * (S + S / 16)];
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = buf[pad(b + r * S)];
+    }
+}
+template <int R, int S>
+__device__ __forceinline__ void sstore(cx<float>* buf, int base, const cx<float>* v) {
+    if constexpr (S % 16 == 0) {
+        cx<float>* p = buf + pad(base);
+#pragma unroll
+        for (int r = 0; r < R; ++r) p[r * (S + S / 16)] = v[r];
+    } else if constexpr (S == 1 && R == 16) {
+        cx<float>* p = buf + pad(base);  // base is a multiple of 16: no pad slot inside
+#pragma unroll
+        for (int r = 0; r < R; ++r) p[r] = v[r];
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[pad(base + r * S)] = v[r];
+    }
+}
+
+// One pass, shared memory to shared memory, with butterflies b = t + T j
+// (j = 0, 1, ...), each loaded, twiddled, transformed and stored before the
+// next.  The twiddles of butterfly b are the powers of w_{NS R}^{b mod NS};
+// when NS divides T every butterfly of the thread has the same ones.
+template <int L, int R, int NS, int T>
+__device__ __forceinline__ void seq_pass(const cx<float>* src, cx<float>* dst, int t, const Tw& tw) {
+    constexpr int NB = L / R;
+    constexpr int IT = (NB + T - 1) / T;
+    constexpr bool shared_k = (T % NS) == 0;
+    cx<float> p[R];
+    if constexpr (NS > 1 && shared_k) powers<R>(tw.get<NS * R>(t % NS), p);
+#pragma unroll 1
+    for (int j = 0; j < IT; ++j) {
+        const int b = t + T * j;
+        if (IT * T == NB || b < NB) {
+            cx<float> v[R];
+            sload<R, NB>(v, src, b);
+            const int k = (NS > 1) ? b % NS : 0;
+            if constexpr (NS > 1) {
+                if constexpr (!shared_k) powers<R>(tw.get<NS * R>(k), p);
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[r] = cmul(v[r], p[r]);
+            }
+            dft<R>(v);
+            sstore<R, NS>(dst, (b - k) * R + k, v);
+        }
+    }
+}
+
+// Last-pass butterfly of thread t in a group of T threads (one butterfly per
+// thread, NB = T).  Within each aligned run of 2H lanes (H = min(T, 32) / 2)
+// lane j of the first half takes butterfly j' and lane j of the second half
+// its mirror NB - j' (j' = (t / 2H) H + j), so that mirror partners are
+// lanes t and t ^ H of one warp; j' = 0 pairs the two self-mirrored
+// butterflies 0 and NB/2.
+template <int T>
+__device__ __forceinline__ int last_b(int t) {
+    constexpr int H = (T < 32 ? T : 32) / 2;
+    const int j = (t / (2 * H)) * H + t % H;
+    return ((t / H) & 1) == 0 ? j : (j == 0 ? T / 2 : T - j);
+}
+
+// Last pass (Ns = L/R): butterfly b, loaded from `src`, twiddled by the
+// powers of w_L^b, transformed; v[s] is bin b + s L/R.
+template <int L, int R>
+__device__ __forceinline__ void last_pass(cx<float>* v, const cx<float>* src, int b, const Tw& tw) {
+    constexpr int NB = L / R;
+    cx<float> p[R];
+    powers<R>(tw.get<L>(b), p);
+    sload<R, NB>(v, src, b);
+#pragma unroll
+    for (int r = 1; r < R; ++r) v[r] = cmul(v[r], p[r]);
+    dft<R>(v);
+}
+
+// ------------------------------------------------------------ the product
+
+// Spectral product at bin k: S_k = a, S_{L-k} = c; returns
+// P_k = conj(H_k)/L X_k^{m-1} (H, X unpacked from S, e = m - 1, sc = 2^-m / L)
+// and adds Re(P_k X_k) to acc when alpha is wanted.
+template <bool F64>
+__device__ __forceinline__ cx<float> product(cx<float> a, cx<float> c, int e, float sc, bool wa, double& acc) {
+    if constexpr (F64) {
+        const double hx = (double)a.x + c.x, hy = (double)a.y - c.y;
+        const cx<double> X = mk<double>((double)a.y + c.y, (double)c.x - a.x);
+        cx<double> p = mk<double>(hx * sc, -hy * sc);
+        if (e & 1) p = cmul(p, X);
+        if (e & 6) {
+            const cx<double> X2 = cmul(X, X);
+            if (e & 2) p = cmul(p, X2);
+            if (e & 4) p = cmul(p, cmul(X2, X2));
+        }
+        if (wa) acc += 0.5 * (p.x * X.x - p.y * X.y);
+        return mk<float>((float)p.x, (float)p.y);
+    } else {
+        const cx<float> X = mk<float>(a.y + c.y, c.x - a.x);
+        cx<float> p = mk<float>((a.x + c.x) * sc, (c.y - a.y) * sc);
+        if (e & 1) p = cmul(p, X);
+        if (e & 6) {
+            const cx<float> X2 = cmul(X, X);
+            if (e & 2) p = cmul(p, X2);
+            if (e & 4) p = cmul(p, cmul(X2, X2));
+        }
+        if (wa) acc += (double)(0.5f * (p.x * X.x - p.y * X.y));
+        return p;
+    }
+}
+
+// Barrier of one group: named barrier for multi-warp groups, the warp's for
+// groups within a warp (every lane runs the same code, padded with empty
+// jobs, so the whole warp always arrives).
+template <int T>
+__device__ __forceinline__ void gsync(int g) {
+    if constexpr (T >= 64) {
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "n"(T) : "memory");
+    } else {
+        __syncwarp();
+    }
+}
+
+// Sum of one double over the T threads of a group (valid in thread 0 of the group).
+template <int T>
+__device__ __forceinline__ double group_sum(double v, double* red, int g, int t) {
+#pragma unroll
+    for (int o = (T < 32 ? T : 32) / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if constexpr (T > 32) {
+        if ((t & 31) == 0) red[g * (T / 32) + (t >> 5)] = v;
+        gsync<T>(g);
+        double s = 0.0;
+        if (t == 0)
+            for (int i = 0; i < T / 32; ++i) s += red[g * (T / 32) + i];
+        gsync<T>(g);
+        return s;
+    }
+    return v;
+}
+
+// Kernel arguments, kept in shared memory for the item functions.
+struct Params {
+    const FastItem* items;
+    const FastJob* jobs;
+    const float* h;
+    const float* x;
+    float* y;
+    float* alpha;
+    int* ctr;
+    int nitems;
+    int after;  // the item after the next one (claimed during the current item)
+};
+__shared__ Params fp_par;
+
+// One item: every group of the block runs one pair job of length L.
+// `staged`: the buffer (0/1) into which the previous item already copied
+// this job's first input, or -1.  `next`: the index of the block's next
+// item; when it has the same length its first input is staged here, into
+// the buffer returned (-1 otherwise).
+template <int L, bool F64>
+__device__ __noinline__ int run_item(int first, int staged, int next) {
+    constexpr int R = rlast(L), T = nthr(L), Q = L / R, GS = L + L / 16;
+    constexpr int QA = q0(Q), QB = q1(Q);  // power-of-two passes (QB == 1: none)
+    constexpr int H = (T < 32 ? T : 32) / 2;  // mirror partner: lane ^ H
+    const Params& c = fp_par;
+    const Tw tw;
+    const int g = threadIdx.x / T, t = threadIdx.x % T;
+    const FastJob& J = c.jobs[first + g];
+    auto buf = [&](int i) { return sm_buf(i) + g * GS; };
+    const bool wa = c.alpha != nullptr;
+    const int b = last_b<T>(t);
+    const bool self0 = b == 0, selfh = b == T / 2;  // self-mirrored butterflies
+    cx<float> v[R];
+    cx<float>* const st = sm_stash() + threadIdx.x;  // P_A, slot s at st[s * BLOCK]
+    double aA = 0.0, aB = 0.0;
+    int after = 0;
+    if (threadIdx.x == 0) after = atomicAdd(c.ctr, 1) + (int)gridDim.x;  // stored at the end
+
+    int cur = staged;
+    if (cur < 0) {
+        cur = 1;
+        stage<L, T>(buf(cur), c.h + J.hA, J.dA, c.x + J.xA, J.nA, t);
+        stage_wait();
+        gsync<T>(g);
+    }
+    // forward transforms of h~ + i x~ (tensor A, then B) and their spectral
+    // products; after B, the thread's stash slots hold Q = P_A + i P_B on its bins
+#pragma unroll 1
+    for (int tensor = 0; tensor < 2; ++tensor) {
+        const bool B = tensor == 1;
+        const int m = B ? J.mB : J.mA;
+        seq_pass<L, QA, 1, T>(buf(cur), buf(cur ^ 1), t, tw);
+        gsync<T>(g);
+        cur ^= 1;
+        if constexpr (QB > 1) {
+            seq_pass<L, QB, QA, T>(buf(cur), buf(cur ^ 1), t, tw);
+            gsync<T>(g);
+            cur ^= 1;
+        }
+        // the other buffer is free: tensor B's input streams in meanwhile
+        if (!B) stage<L, T>(buf(cur ^ 1), c.h + J.hB, J.dB, c.x + J.xB, J.nB, t);
+        last_pass<L, R>(v, buf(cur), b, tw);
+        // bin b + s NB pairs with bin L - (b + s NB): the partner lane's
+        // slot R-1-s, or this lane's own slot for the self-mirrored butterflies
+        const float sc = ldexpf(1.0f / (float)L, -m);
+        const int e = m - 1;
+        double a = 0.0;
+#pragma unroll
+        for (int s = 0; s < R; ++s) {
+            const cx<float> o = v[R - 1 - s];
+            cx<float> cpart = mk<float>(__shfl_xor_sync(0xffffffffu, o.x, H), __shfl_xor_sync(0xffffffffu, o.y, H));
+            cpart = sel(self0, v[(R - s) % R], sel(selfh, o, cpart));
+            const cx<float> p = product<F64>(v[s], cpart, e, sc, wa, a);
+            // tensor A: P_A; tensor B: Q = P_A + i P_B (v still holds S_B)
+            st[s * BLOCK] = B ? plus_i(st[s * BLOCK], p) : p;
+        }
+        if (!B) {
+            aA = a;
+            stage_wait();
+            gsync<T>(g);
+            cur ^= 1;
+        } else {
+            aB = a;
+        }
+    }
+
+    int staged_next = -1;
+    // y~ = fft(P_A + i P_B): first pass (radix R, butterfly b) from
+    // registers, then the power-of-two passes, the last one storing y.
+    if (c.y != nullptr) {
+#pragma unroll
+        for (int s = 0; s < R; ++s) v[s] = st[s * BLOCK];
+        dft<R>(v);
+        sstore<R, 1>(buf(cur ^ 1), b * R, v);
+        gsync<T>(g);
+        cur ^= 1;
+        if constexpr (QB > 1) {
+            seq_pass<L, QB, R, T>(buf(cur), buf(cur ^ 1), t, tw);
+            gsync<T>(g);
+            cur ^= 1;
+        }
+    }
+    // the next item's first input, when it has this length, into the free buffer
+    if (next < c.nitems) {
+        const FastItem N = c.items[next];
+        if (N.L == L) {
+            const FastJob& K = c.jobs[N.first + g];
+            staged_next = cur ^ 1;
+            stage<L, T>(buf(staged_next), c.h + K.hA, K.dA, c.x + K.xA, K.nA, t);
+        }
+    }
+    if (c.y != nullptr) {
+        // last pass (radix QA, Ns = L/QA, butterflies b = t + T j); output
+        // bin b + s Ns, stored when below n
+        constexpr int NBL = L / QA;
+        constexpr int IT = (NBL + T - 1) / T;
+        const int nA = J.nA, nB = J.nB, nmax = max(nA, nB);
+        float* yA = c.y + J.yA;
+        float* yB = c.y + J.yB;
+#pragma unroll 1
+        for (int j = 0; j < IT; ++j) {
+            const int bl = t + T * j;
+            if ((IT * T == NBL || bl < NBL) && bl < nmax) {
+                cx<float> w[QA];
+                last_pass<L, QA>(w, buf(cur), bl, tw);
+#pragma unroll
+                for (int s = 0; s < QA; ++s) {
+                    const int i0 = bl + s * NBL;
+                    if (i0 < nA) yA[i0] = w[s].x;
+                    if (i0 < nB) yB[i0] = w[s].y;
+                }
+            }
+        }
+    }
+    if (wa) {
+        const double sA = group_sum<T>(aA, sm_red(), g, t);
+        const double sB = group_sum<T>(aB, sm_red(), g, t);
+        if (t == 0) {
+            if (J.iA >= 0) c.alpha[J.iA] = (float)sA;
+            if (J.iB >= 0) c.alpha[J.iB] = (float)sB;
+        }
+    }
+    if (threadIdx.x == 0) fp_par.after = after;
+    return staged_next;
+}
+
+template <bool F64>
+__global__ void __launch_bounds__(BLOCK, HK_FAST_MIN_BLOCKS)
+    fast_fwd_kernel(const FastItem* __restrict__ items, int nitems, const FastJob* __restrict__ jobs,
+                    const float* __restrict__ h, const float* __restrict__ x, float* __restrict__ y,
+                    float* __restrict__ alpha, const cx<float>* __restrict__ tw2, const cx<float>* __restrict__ tw3,
+                    int* ctr) {
+    cx<float>* t2 = sm_t2();
+    cx<float>* t3 = sm_t3();
+    for (int i = threadIdx.x; i < TW2; i += BLOCK) t2[i] = ldg_cx(tw2 + i);
+    for (int i = threadIdx.x; i < TW3; i += BLOCK) t3[i] = ldg_cx(tw3 + i);
+    if (threadIdx.x == 0) {
+        fp_par.items = items;
+        fp_par.jobs = jobs;
+        fp_par.h = h;
+        fp_par.x = x;
+        fp_par.y = y;
+        fp_par.alpha = alpha;
+        fp_par.ctr = ctr;
+        fp_par.nitems = nitems;
+        // items: blockIdx.x first, then claimed from the counter; the claim
+        // of the item after the next one overlaps the current item
+        fp_par.after = atomicAdd(ctr, 1) + (int)gridDim.x;
+    }
+    __syncthreads();
+    int it = blockIdx.x, next = fp_par.after;
+    int staged = -1;
+    __syncthreads();
+    while (it < nitems) {
+        const FastItem I = items[it];
+        switch (I.L) {
+            case 4096: staged = run_item<4096, F64>(I.first, staged, next); break;
+            case 3072: staged = run_item<3072, F64>(I.first, staged, next); break;
+            case 2048: staged = run_item<2048, F64>(I.first, staged, next); break;
+            case 1536: staged = run_item<1536, F64>(I.first, staged, next); break;
+            case 1024: staged = run_item<1024, F64>(I.first, staged, next); break;
+            case 768: staged = run_item<768, F64>(I.first, staged, next); break;
+            case 512: staged = run_item<512, F64>(I.first, staged, next); break;
+            case 384: staged = run_item<384, F64>(I.first, staged, next); break;
+            case 256: staged = run_item<256, F64>(I.first, staged, next); break;
+            case 192: staged = run_item<192, F64>(I.first, staged, next); break;
+            case 128: staged = run_item<128, F64>(I.first, staged, next); break;
+            case 96: staged = run_item<96, F64>(I.first, staged, next); break;
+            case 64: staged = run_item<64, F64>(I.first, staged, next); break;
+            case 48: staged = run_item<48, F64>(I.first, staged, next); break;
+            case 32: staged = run_item<32, F64>(I.first, staged, next); break;
+            default: staged = -1; break;
+        }
+        // the staged copies must land before the next item reads them
+        if (staged >= 0) stage_wait();
+        __syncthreads();
+        it = next;
+        next = fp_par.after;
+        __syncthreads();
+    }
+    // copies staged for an item that does not exist are never issued
+    // (run_item stages only for next < nitems)
+    // the last block to finish re-arms the counter for the next launch
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(ctr + 1, 1) == (int)gridDim.x - 1) {
+            ctr[0] = 0;
+            ctr[1] = 0;
+            __threadfence();
+        }
+    }
+}
+
+}  // namespace fp
+
+bool fast_length_ok(int L) {
+    switch (L) {
+        case 4096: case 3072: case 2048: case 1536: case 1024: case 768: case 512: case 384:
+        case 256: case 192: case 128: case 96: case 64: case 48: case 32: return true;
+        default: return false;
+    }
+}
+
+int fast_length(int64_t d) {
+    static const int lens[] = {32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048, 3072, 4096};
+    for (int L : lens)
+        if (L >= d) return L;
+    return 0;
+}
+
+int fast_jobs_per_item(int L) { return fp::BLOCK / fp::nthr(L); }
+
+size_t fast_smem_bytes() {
+    return fp::RED * sizeof(double) +
+           ((size_t)fp::TW2 + fp::TW3 + 2 * (size_t)fp::BUF + (size_t)fp::STASH * fp::BLOCK) * sizeof(cx<float>);
+}
+
+cudaError_t launch_fast_forward(const FastItem* items, int nitems, int grid, const FastJob* jobs, const void* h,
+                                const void* x, void* y, void* alpha, const void* t2, const void* t3, int* ctr,
+                                int flags, cudaStream_t st) {
+    const size_t smem = fast_smem_bytes();
+    const bool f64 = (flags & HANKEL_FP64_POWER) != 0;
+    auto k = f64 ? fp::fast_fwd_kernel<true> : fp::fast_fwd_kernel<false>;
+    static std::mutex mu;
+    static bool done[2][64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (dev < 64 && !done[f64][dev]) {
+            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            // shared memory for the resident blocks only; the rest stays L1
+            // (spill slots, descriptors)
+            int maxsm = 0;
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+            if (e == cudaSuccess && maxsm > 0) {
+                const size_t want = (size_t)HK_FAST_MIN_BLOCKS * (smem + 1024);
+                const int pct = (int)std::min<size_t>(100, (want * 100 + maxsm - 1) / maxsm);
+                e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+            }
+            if (e != cudaSuccess) return e;
+            done[f64][dev] = true;
+        }
+    }
+    k<<<grid, fp::BLOCK, smem, st>>>(items, nitems, jobs, (const float*)h, (const float*)x, (float*)y, (float*)alpha,
+                                     (const cx<float>*)t2, (const cx<float>*)t3, ctr);
+    return cudaGetLastError();
+}
+
+int fast_blocks_per_sm() { return HK_FAST_MIN_BLOCKS; }
+
+}  // namespace hk

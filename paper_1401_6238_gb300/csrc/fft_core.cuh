@@ -222,6 +222,42 @@ struct DFT<T, 5> : DFTodd<T, 5> {};
 template <typename T>
 struct DFT<T, 7> : DFTodd<T, 7> {};
 
+// Composite radix N = N1 N2 with coprime factors by the prime-factor
+// (Good-Thomas) map: input n = (N2 n1 + N1 n2) mod N, output
+// k = (N2 e1 k1 + N1 e2 k2) mod N with e1 = N2^-1 mod N1, e2 = N1^-1 mod N2,
+// so that w_N^{nk} = w_N1^{n1 k1} w_N2^{n2 k2}: N2 transforms of size N1,
+// then N1 of size N2, with no twiddle factors between them.
+__host__ __device__ constexpr int inv_mod(int a, int m) {
+    int r = 1;
+    while ((a * r) % m != 1) ++r;
+    return r;
+}
+template <typename T, int N1, int N2>
+struct DFTpfa {
+    static __device__ __forceinline__ void run(cx<T>* a) {
+        constexpr int N = N1 * N2;
+        constexpr int e1 = inv_mod(N2 % N1, N1), e2 = inv_mod(N1 % N2, N2);
+        cx<T> A[N2][N1];
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) {
+#pragma unroll
+            for (int n1 = 0; n1 < N1; ++n1) A[n2][n1] = a[(N2 * n1 + N1 * n2) % N];
+            DFT<T, N1>::run(A[n2]);
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) {
+            cx<T> B[N2];
+#pragma unroll
+            for (int n2 = 0; n2 < N2; ++n2) B[n2] = A[n2][k1];
+            DFT<T, N2>::run(B);
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) a[(N2 * e1 * k1 + N1 * e2 * k2) % N] = B[k2];
+        }
+    }
+};
+template <typename T>
+struct DFT<T, 12> : DFTpfa<T, 4, 3> {};
+
 // ------------------------------------------------------------- shared memory
 // One padding slot every 16 elements spreads strided butterfly accesses over
 // the banks.

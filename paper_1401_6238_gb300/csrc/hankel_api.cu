@@ -188,6 +188,19 @@ struct hankel_plan_s {
     std::vector<hk::RealLaunch> fwd_launches, bwd_launches;
     hk::RealJob* d_fwd = nullptr;
     hk::RealJob* d_bwd = nullptr;
+    // persistent forward kernel (FP32, one vector per tensor): the tensors
+    // whose generating length fits its transforms run there, the rest on
+    // the per-length launches above
+    bool fast = false;
+    std::vector<hk::FastJob> fast_jobs;
+    std::vector<hk::FastItem> fast_items;
+    hk::FastJob* d_fast_jobs = nullptr;
+    hk::FastItem* d_fast_items = nullptr;
+    int* d_fast_ctr = nullptr;
+    void* d_fast_tw = nullptr;  // two-level tables of w_4096 and w_3072 (FP32 complex)
+    size_t fast_tw3 = 0;        // byte offset of the w_3072 table
+    int fast_grid = 0;
+    int64_t fast_pairs = 0;  // pair jobs with at least one tensor (the rest pad items)
     // general path (complex data, distinct vectors, BHHB)
     hk::GeneralPlan* gen = nullptr;
     // twiddle tables and workspace
@@ -237,6 +250,10 @@ void free_plan(hankel_plan_s* p) {
     if (!p) return;
     cudaFree(p->d_fwd);
     cudaFree(p->d_bwd);
+    cudaFree(p->d_fast_jobs);
+    cudaFree(p->d_fast_items);
+    cudaFree(p->d_fast_ctr);
+    cudaFree(p->d_fast_tw);
     cudaFree(p->d_multi);
     cudaFree(p->d_tw);
     cudaFree(p->d_ws);
@@ -413,6 +430,89 @@ int split_length(const hankel_plan_s* p, int L) {
     return L / 2;
 }
 
+// Pair jobs and work items of the persistent forward kernel for the tensors
+// marked in `sel`: tensors of one FFT length in pairs, each length's jobs
+// padded with empty slots to whole items, items longest length first.
+hankel_status build_fast(hankel_plan_s* p, const std::vector<char>& sel) {
+    const int64_t count = (int64_t)p->descs.size();
+    std::vector<std::pair<int, int64_t>> byL;
+    for (int64_t i = 0; i < count; ++i)
+        if (sel[i]) {
+            const hankel_desc& d = p->descs[i];
+            byL.emplace_back(hk::fast_length((int64_t)d.n[0] * d.m - d.m + 1), i);
+        }
+    if (byL.empty()) return HANKEL_OK;
+    std::stable_sort(byL.begin(), byL.end(),
+                     [](const std::pair<int, int64_t>& a, const std::pair<int, int64_t>& b) { return a.first > b.first; });
+    hk::FastJob empty;
+    std::memset(&empty, 0, sizeof(empty));
+    empty.mA = empty.mB = 2;
+    empty.iA = empty.iB = -1;
+    auto put = [&](hk::FastJob& J, int64_t i, bool B) {
+        const hankel_desc& d = p->descs[i];
+        const int dl = (int)((int64_t)d.n[0] * d.m - d.m + 1);
+        if (!B) {
+            J.mA = d.m; J.nA = d.n[0]; J.dA = dl; J.iA = (int)i;
+            J.hA = d.h_off; J.xA = d.x_off[0]; J.yA = d.y_off;
+        } else {
+            J.mB = d.m; J.nB = d.n[0]; J.dB = dl; J.iB = (int)i;
+            J.hB = d.h_off; J.xB = d.x_off[0]; J.yB = d.y_off;
+        }
+    };
+    p->fast_jobs.clear();
+    p->fast_items.clear();
+    p->fast_pairs = 0;
+    for (size_t k = 0; k < byL.size();) {
+        const int L = byL[k].first;
+        const int G = hk::fast_jobs_per_item(L);
+        size_t e = k;
+        while (e < byL.size() && byL[e].first == L) ++e;
+        std::vector<hk::FastJob> js;
+        for (size_t q = k; q < e; q += 2) {
+            hk::FastJob J = empty;
+            put(J, byL[q].second, false);
+            if (q + 1 < e) put(J, byL[q + 1].second, true);
+            js.push_back(J);
+            ++p->fast_pairs;
+        }
+        while (js.size() % G) js.push_back(empty);
+        for (size_t q = 0; q < js.size(); q += G)
+            p->fast_items.push_back(hk::FastItem{L, (int32_t)(p->fast_jobs.size() + q)});
+        p->fast_jobs.insert(p->fast_jobs.end(), js.begin(), js.end());
+        k = e;
+    }
+    int sms = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    p->fast_grid = (int)std::min<int64_t>((int64_t)p->fast_items.size(), (int64_t)sms * hk::fast_blocks_per_sm());
+    if ((e = cudaMalloc(&p->d_fast_jobs, p->fast_jobs.size() * sizeof(hk::FastJob))) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc(jobs)");
+    if ((e = cudaMalloc(&p->d_fast_items, p->fast_items.size() * sizeof(hk::FastItem))) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc(jobs)");
+    if ((e = cudaMalloc(&p->d_fast_ctr, 2 * sizeof(int))) != cudaSuccess) return cuda_fail(e, "cudaMalloc(counter)");
+    hk::FftPlan P2, P3;
+    std::memset(&P2, 0, sizeof(P2));
+    std::memset(&P3, 0, sizeof(P3));
+    P2.L = 4096;
+    P3.L = 3072;
+    const int n2 = hk::stage_twiddle_count(P2), n3 = hk::stage_twiddle_count(P3);
+    if ((e = cudaMalloc(&p->d_fast_tw, (size_t)(n2 + n3) * 2 * sizeof(float))) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc(twiddles)");
+    p->fast_tw3 = (size_t)n2 * 2 * sizeof(float);
+    e = cudaMemcpy(p->d_fast_jobs, p->fast_jobs.data(), p->fast_jobs.size() * sizeof(hk::FastJob),
+                   cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p->d_fast_items, p->fast_items.data(), p->fast_items.size() * sizeof(hk::FastItem),
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(p->d_fast_ctr, 0, 2 * sizeof(int));
+    if (e == cudaSuccess) e = hk::launch_stage_twiddles(false, p->d_fast_tw, P2, 0);
+    if (e == cudaSuccess) e = hk::launch_stage_twiddles(false, (char*)p->d_fast_tw + p->fast_tw3, P3, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "fast path set-up");
+    p->fast = true;
+    return HANKEL_OK;
+}
+
 hankel_status build_real_path(hankel_plan_s* p) {
     const int64_t count = (int64_t)p->descs.size();
     const bool dbl = is_double(p->dtype);
@@ -450,7 +550,21 @@ hankel_status build_real_path(hankel_plan_s* p) {
     std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return p->Lof[a] < p->Lof[b]; });
     p->fwd_jobs.clear();
     p->bwd_jobs.clear();
-    for (size_t k = 0; k < order.size();) {
+    // FP32 forward products whose generating length fits the persistent
+    // kernel's transforms run there
+    const bool fast_ok = p->dtype == HANKEL_R32 &&
+                         !(p->flags & (HANKEL_STORE_SPECTRA | HANKEL_ONE_PER_LAUNCH | HANKEL_ANTICIRCULANT));
+    std::vector<char> on_fast(count, 0);
+    if (fast_ok)
+        for (int64_t i = 0; i < count; ++i) {
+            const hankel_desc& d = p->descs[i];
+            on_fast[i] = hk::fast_length((int64_t)d.n[0] * d.m - d.m + 1) > 0;
+        }
+    std::vector<int64_t> fwd_order;
+    for (int64_t a : order)
+        if (!on_fast[a]) fwd_order.push_back(a);
+    for (size_t k = 0; k < fwd_order.size();) {
+        const std::vector<int64_t>& order = fwd_order;
         hk::RealJob J;
         std::memset(&J, 0, sizeof(J));
         const int64_t a = order[k];
@@ -523,8 +637,13 @@ hankel_status build_real_path(hankel_plan_s* p) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(jobs)");
     e = cudaMemcpy(p->d_bwd, p->bwd_jobs.data(), p->bwd_jobs.size() * jb, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(jobs)");
-    const hankel_status ss = make_streams(p, opl ? 0 : std::max(p->fwd_launches.size(), p->bwd_launches.size()));
+    const size_t nfwd = p->fwd_launches.size() + (fast_ok ? 1 : 0);
+    const hankel_status ss = make_streams(p, opl ? 0 : std::max(nfwd, p->bwd_launches.size()));
     if (ss != HANKEL_OK) return ss;
+    if (fast_ok) {
+        const hankel_status fs = build_fast(p, on_fast);
+        if (fs != HANKEL_OK) return fs;
+    }
     p->ws_bytes = (size_t)std::max<int64_t>(ws, 1) * 2 * real_size(p->dtype);
     e = cudaMalloc(&p->d_ws, p->ws_bytes);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(workspace)");
@@ -1066,9 +1185,39 @@ hankel_status hankel_txv(hankel_plan_t p, const void* h, const void* x, void* y,
             return hk::launch_real_multi(dbl, lc, p->d_multi, h, x, y, alpha, p->d_tw, s);
         });
     if (!p->real_path) return hk::general_forward(p->gen, h, x, y, alpha, st, g_err);
-    return run_forked(p, p->fwd_launches, st, [&](const hk::RealLaunch& lc, cudaStream_t s) {
+    auto fwd = [&](const hk::RealLaunch& lc, cudaStream_t s) {
         return hk::launch_real_forward(dbl, lc, p->d_fwd, h, x, y, alpha, p->d_tw, p->d_ws, (int)p->flags, s);
-    });
+    };
+    if (!p->fast) return run_forked(p, p->fwd_launches, st, fwd);
+    // the per-length launches (queued first) on the plan's streams, the
+    // persistent kernel on the caller's stream, joined back into it
+    auto fast = [&](cudaStream_t s) {
+        const char* t2 = (const char*)p->d_fast_tw;
+        return hk::launch_fast_forward(p->d_fast_items, (int)p->fast_items.size(), p->fast_grid, p->d_fast_jobs, h, x,
+                                       y, alpha, t2, t2 + p->fast_tw3, p->d_fast_ctr, (int)p->flags, s);
+    };
+    cudaError_t e;
+    if (p->fwd_launches.empty() || p->streams.empty()) {
+        for (auto& lc : p->fwd_launches)
+            if ((e = fwd(lc, st)) != cudaSuccess) return cuda_fail(e, "kernel launch");
+        if ((e = fast(st)) != cudaSuccess) return cuda_fail(e, "kernel launch");
+        return HANKEL_OK;
+    }
+    const size_t n = std::min(p->streams.size(), p->fwd_launches.size());
+    if ((e = cudaEventRecord(p->events[0], st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    for (size_t i = 0; i < n; ++i)
+        if ((e = cudaStreamWaitEvent(p->streams[i], p->events[0], 0)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamWaitEvent");
+    for (size_t i = 0; i < p->fwd_launches.size(); ++i)
+        if ((e = fwd(p->fwd_launches[i], p->streams[i % n])) != cudaSuccess) return cuda_fail(e, "kernel launch");
+    if ((e = fast(st)) != cudaSuccess) return cuda_fail(e, "kernel launch");
+    for (size_t i = 0; i < n; ++i) {
+        if ((e = cudaEventRecord(p->events[1 + i], p->streams[i])) != cudaSuccess)
+            return cuda_fail(e, "cudaEventRecord");
+        if ((e = cudaStreamWaitEvent(st, p->events[1 + i], 0)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamWaitEvent");
+    }
+    return HANKEL_OK;
 }
 
 hankel_status hankel_txv_host(hankel_plan_t p, const void* h, const void* x, void* y, void* alpha,
@@ -1224,8 +1373,8 @@ hankel_status hankel_plan_query(hankel_plan_t p, hankel_plan_info* info) {
         info->distinct_lengths = (int64_t)p->tw_off.size();
         info->workspace_bytes = 0;
     } else if (p->real_path) {
-        info->jobs = (int64_t)p->fwd_jobs.size();
-        info->launches = (int64_t)p->fwd_launches.size();
+        info->jobs = (int64_t)p->fwd_jobs.size() + p->fast_pairs;
+        info->launches = (int64_t)p->fwd_launches.size() + (p->fast ? 1 : 0);
         info->distinct_lengths = (int64_t)p->tw_off.size();
         info->workspace_bytes = (int64_t)p->ws_bytes;
     } else {

@@ -78,4 +78,18 @@ struct RealLaunch {
     int32_t nthr, split, Lmax, arrays;  // split: the jobs are split jobs (two blocks each)
 };
 
+// Persistent forward kernel (fast_path.cu): a pair job of two real square
+// one-vector tensors A and B with one FFT length; iA < 0 marks an empty slot
+// and iB < 0 a missing partner (both then read and write nothing).
+struct FastJob {
+    int32_t mA, nA, dA, iA;
+    int32_t mB, nB, dB, iB;
+    int64_t hA, xA, yA, hB, xB, yB;
+};
+// One work item of the persistent kernel: the jobs [first, first + G) of FFT
+// length L, G = jobs per item of that length (one per thread group of a block).
+struct FastItem {
+    int32_t L, first;
+};
+
 }  // namespace hk

@@ -1,0 +1,168 @@
+"""GPU parity of the persistent FP32 forward kernel (real square tensors with
+one vector per tensor, y = H x^{m-1} and alpha = H x^m, Section 3) against
+the FP64 oracle, through the C ABI.
+
+The kernel runs every tensor whose generating length d fits one of its FFT
+lengths (2^k and 3 * 2^k, 32..4096); longer ones run on the per-length
+launches in the same call.  Inputs use the benchmark's scaling (h ~ N(0, 1/d),
+unit-norm x), at which the FP32 bound is 1e-5 relative in the infinity norm
+for every order tested here.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1401_6238_gb300 import hankel as hk
+from paper_1401_6238_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-5
+FAST_LENGTHS = [32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048, 3072, 4096]
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    hk.load()
+    return torch.device("cuda:0")
+
+
+def scaled_tensors(shapes, seed):
+    """Tensors (m, n) with h ~ N(0, 1/d) and unit-norm x, packed."""
+    rng = np.random.default_rng(seed)
+    orders, dims, hs, xs = [], [], [], []
+    for m, n in shapes:
+        d = m * (n - 1) + 1
+        x = rng.standard_normal(n)
+        orders.append(m)
+        dims.append(n)
+        hs.append(rng.standard_normal(d) / np.sqrt(d))
+        xs.append(x / np.linalg.norm(x))
+    return wl.pack_square(orders, dims, hs, xs)
+
+
+def run(b, flags=hk.SAME_X, want_y=True, want_alpha=True, dev=None, calls=1):
+    plan = hk.Plan(hk.batch_descs(b), hk.R32, flags)
+    H = torch.tensor(b.h, dtype=torch.float32, device=dev)
+    X = torch.tensor(b.x, dtype=torch.float32, device=dev)
+    outs = []
+    for _ in range(calls):
+        Y = torch.full((b.y_len,), float("nan"), dtype=torch.float32, device=dev) if want_y else None
+        A = torch.full((len(b),), float("nan"), dtype=torch.float32, device=dev) if want_alpha else None
+        plan.txv(H, X, Y, A)
+        torch.cuda.synchronize()
+        outs.append((Y.cpu().numpy().astype(np.float64) if want_y else None,
+                     A.cpu().numpy().astype(np.float64) if want_alpha else None))
+    info = plan.info
+    plan.close()
+    return outs, info
+
+
+def check(b, y, a, tol=TOL32):
+    worst = 0.0
+    for i in range(len(b)):
+        m, n, h, x = b.tensor(i)
+        ref = oracle.fast_y(h, [x] * (m - 1), [n] * m).real
+        if y is not None:
+            got = y[b.y_off[i]: b.y_off[i] + n]
+            e = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+            worst = max(worst, e)
+            assert e <= tol, (i, m, n, e)
+        if a is not None:
+            a_ref = float(np.dot(x, ref))
+            scale = np.max(np.abs(ref)) * np.sum(np.abs(x))
+            assert abs(a[i] - a_ref) <= tol * scale, (i, m, n, a[i], a_ref)
+    return worst
+
+
+def shapes_for_length(L, orders):
+    """(m, n) pairs whose generating length d = m (n - 1) + 1 lands on FFT
+    length L: the smallest d above the previous length, the largest d <= L,
+    and one in between, for each order m that reaches L."""
+    i = FAST_LENGTHS.index(L)
+    lo = FAST_LENGTHS[i - 1] if i > 0 else 0
+    out = []
+    for m in orders:
+        ns = [n for n in range(1, L + 1) if lo < m * (n - 1) + 1 <= L]
+        if ns:
+            out += [(m, n) for n in sorted({ns[0], ns[len(ns) // 2], ns[-1]})]
+    return out
+
+
+@pytest.mark.parametrize("L", FAST_LENGTHS)
+def test_every_length(dev, L):
+    shapes = shapes_for_length(L, [2, 3, 4, 5])
+    assert shapes
+    b = scaled_tensors(shapes, seed=L)
+    for i in range(len(b)):
+        m, n, _, _ = b.tensor(i)
+        assert m * (n - 1) + 1 <= L
+    (y, a) = run(b, dev=dev)[0][0]
+    worst = check(b, y, a)
+    print("L=%d: %d tensors, worst rel err %.2e" % (L, len(b), worst))
+
+
+@pytest.mark.parametrize("m", [6, 7, 8])
+def test_high_orders(dev, m):
+    # orders above the benchmark's, FFT lengths of both families
+    shapes = [(m, n) for n in (3, 5, 9, 17, 64, 100, 200, 300, 400, 511)]
+    b = scaled_tensors(shapes, seed=100 + m)
+    (y, a) = run(b, dev=dev)[0][0]
+    check(b, y, a)
+
+
+def test_many_jobs_per_item(dev):
+    # 131 tensors of FFT length 64 (64 pair jobs per item): two full items,
+    # a partly filled third one and a tensor with no partner
+    shapes = [(3, 16 + (i % 6)) for i in range(131)]
+    b = scaled_tensors(shapes, seed=7)
+    (y, a) = run(b, dev=dev)[0][0]
+    check(b, y, a)
+
+
+def test_fp64_spectrum_products(dev):
+    b = wl.batched_square(count=40, seed=33, orders=(4, 5), n_lo=300, n_hi=1024)
+    (y, a) = run(b, flags=hk.SAME_X | hk.FP64_POWER, dev=dev)[0][0]
+    check(b, y, a)
+
+
+def test_y_only_and_alpha_only(dev):
+    b = wl.batched_square(count=33, seed=34, n_lo=16, n_hi=700)
+    (y, a) = run(b, want_alpha=False, dev=dev)[0][0]
+    assert a is None
+    check(b, y, None)
+    (y, a) = run(b, want_y=False, dev=dev)[0][0]
+    assert y is None
+    check(b, None, a)
+
+
+def test_mixed_with_longer_lengths(dev):
+    # generating lengths above 4096 run on the per-length launches of the
+    # same call; both sets must be right, and the plan reports both launches
+    shapes = [(5, 1000), (5, 1024), (4, 1300), (3, 2000), (5, 900), (3, 700), (4, 300), (3, 40)]
+    b = scaled_tensors(shapes, seed=9)
+    (y, a) = run(b, dev=dev)[0][0]
+    check(b, y, a)
+
+
+def test_repeat_calls_identical(dev):
+    # the work counter re-arms itself: repeated calls give the same bits
+    b = wl.batched_square(count=300, seed=35, n_lo=16, n_hi=1024)
+    outs, info = run(b, dev=dev, calls=3)
+    for y, a in outs[1:]:
+        np.testing.assert_array_equal(y, outs[0][0])
+        np.testing.assert_array_equal(a, outs[0][1])
+    check(b, outs[0][0], outs[0][1])
+
+
+def test_benchmark_shapes_one_launch(dev):
+    # the benchmark's shape mix restricted to generating lengths <= 4096
+    # (orders 3 and 4): a single persistent launch
+    b = wl.batched_square(count=512, seed=36, orders=(3, 4), n_lo=16, n_hi=1024)
+    outs, info = run(b, dev=dev)
+    assert info["launches"] == 1
+    check(b, outs[0][0], outs[0][1])

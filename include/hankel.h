@@ -290,8 +290,11 @@ hankel_status hankel_txv_backward(hankel_plan_t plan, const void* grad_y, const 
  * A batch whose scratch would exceed the array (the sum over tensors of
  * L * 2 * sizeof(real), plus one twiddle table per distinct L, each rounded
  * up to 256 bytes) is rejected with HANKEL_EINVAL and a message giving the
- * bytes it needs; so are non-square tensors and FFT lengths beyond the
- * shared-memory limit.  No cudaMalloc, cudaFree or allocating library call is
+ * bytes it needs; so are non-square tensors, FFT lengths beyond the
+ * shared-memory limit, and descriptors whose h regions or x regions overlap
+ * (each tensor's gradients are written, not summed as hankel_txv_backward
+ * does for shared storage).  Spectrum products are formed in the data
+ * precision: there is no HANKEL_FP64_POWER option here.  No cudaMalloc, cudaFree or allocating library call is
  * made.  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current: make that first call
  * before any stream capture.  Every call shares the array and overwrites the

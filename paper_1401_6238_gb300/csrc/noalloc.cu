@@ -12,6 +12,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "fft_core.cuh"
@@ -133,6 +134,22 @@ hankel_status scratch_base(void** out) {
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
+// Raise the kernel's dynamic shared-memory limit only when a launch needs
+// more than already granted on this device.
+template <typename T>
+cudaError_t grant_smem(size_t bytes) {
+    static size_t granted[kMaxDevices] = {0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (bytes <= granted[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(static_bwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) granted[dev] = bytes;
+    return e;
+}
+
 template <typename T>
 hankel_status run_static(const hankel_desc* descs, int64_t count, const void* gy, const void* h, const void* x,
                          void* gh, void* gx, cudaStream_t st) {
@@ -184,6 +201,21 @@ hankel_status run_static(const hankel_desc* descs, int64_t count, const void* gy
         used += align256((size_t)L * cs);
         jobs.push_back(J);
     }
+    // each tensor's gradients are written, not summed: descriptors whose h
+    // regions or x regions overlap would race
+    for (int w = 0; w < 2; ++w) {
+        std::vector<std::pair<int64_t, int64_t>> iv;
+        for (const auto& J : jobs)
+            iv.emplace_back(w == 0 ? J.hA : J.xA, (w == 0 ? J.hA : J.xA) + (w == 0 ? J.dA : J.nA));
+        std::sort(iv.begin(), iv.end());
+        for (size_t k = 1; k < iv.size(); ++k)
+            if (iv[k].first < iv[k - 1].second) {
+                set_last_error(std::string("descriptors share ") + (w == 0 ? "h" : "x") +
+                               " storage: this entry point writes each tensor's gradients, so overlapping regions "
+                               "are not allowed (hankel_txv_backward sums them)");
+                return HANKEL_EINVAL;
+            }
+    }
     if (used > (size_t)HANKEL_STATIC_SCRATCH_BYTES) {
         set_last_error("the batch needs " + std::to_string(used) + " bytes of scratch; the static array holds " +
                        std::to_string((long long)HANKEL_STATIC_SCRATCH_BYTES));
@@ -210,8 +242,7 @@ hankel_status run_static(const hankel_desc* descs, int64_t count, const void* gy
         int nthr = 32;
         while (nthr < 512 && nthr < (Lmax + 15) / 16) nthr <<= 1;
         const size_t smem = RED_BYTES + 2 * smem_elems_host(Lmax) * cs;
-        cudaError_t e = cudaFuncSetAttribute(static_bwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = grant_smem<T>(smem);
         if (e == cudaSuccess) {
             static_bwd_kernel<T><<<n, nthr, smem, st>>>(pj, (const T*)gy, (const T*)h, (const T*)x, (T*)gh, (T*)gx,
                                                         Lmax);

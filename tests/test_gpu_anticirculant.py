@@ -184,7 +184,7 @@ def test_block_anticirculant(dev):
     ref = lv.fast_level_y(G, Xs[1:], sizes)
     assert rel(lv.unvec(Y.cpu().numpy(), (n, N)), ref) <= 1e-12
     ar = lv.fast_level_alpha(G, Xs, sizes)
-    assert abs(A.cpu().numpy()[0] - ar) <= 1e-12 * abs(ar) * 10
+    assert abs(A.cpu().numpy()[0] - ar) <= 1e-12 * abs(ar), (A.cpu().numpy()[0], ar)
     # the same through a level-3 multilevel plan with a trivial third level
     md = hk.level_descs([[n] * m, [N] * m, [1] * m], [0], [[0, n * N, 2 * n * N]], [0])
     plan3 = hk.Plan(md, hk.C128, hk.ANTICIRCULANT)

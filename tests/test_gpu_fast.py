@@ -166,3 +166,13 @@ def test_benchmark_shapes_one_launch(dev):
     outs, info = run(b, dev=dev)
     assert info["launches"] == 1
     check(b, outs[0][0], outs[0][1])
+
+
+def test_mixed_orders_same_length(dev):
+    # tensors of one FFT length but different orders are never paired (the
+    # kernel raises both spectra of a pair to one power): every order must
+    # still come out right, including odd counts per (length, order)
+    shapes = [(3, 600), (4, 450), (5, 360), (3, 610), (4, 455), (5, 365), (3, 620), (2, 900), (6, 300)]
+    b = scaled_tensors(shapes, seed=37)
+    (y, a) = run(b, dev=dev)[0][0]
+    check(b, y, a)

@@ -15,7 +15,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TDT = {hk.R32: torch.float32, hk.C64: torch.complex64, hk.R64: torch.float64, hk.C128: torch.complex128}
-TOL = {hk.R32: 2e-5, hk.C64: 2e-5, hk.R64: 1e-11, hk.C128: 1e-11}
+TOL = {hk.R32: 1e-5, hk.C64: 1e-5, hk.R64: 1e-12, hk.C128: 1e-12}
 
 
 @pytest.fixture(scope="module")
@@ -148,16 +148,20 @@ def test_fuzz_case(dev, idx):
             rx = [lv.vec(r) for r in rx]
         if not cplx:
             ref, ar = ref.real, ar.real
-        assert rel(y[y_offs[t]: y_offs[t] + ny], ref) <= tol, (idx, c, "y", t)
+        ey = rel(y[y_offs[t]: y_offs[t] + ny], ref)
+        assert ey <= tol, (idx, c, "y", t, ey)
         scale = np.abs(ref).max() * np.abs(vecs[0]).sum()
-        assert abs(a[t] - ar) <= tol * max(scale, 1e-30) * 10, (idx, c, "alpha", t)
+        ea = abs(a[t] - ar) / max(scale, 1e-30)
+        assert ea <= tol, (idx, c, "alpha", t, ea)
         want_h[h_off[t]: h_off[t] + hsz] += rh
         for p in range(1, m):
             o = x_offs[t][0 if c["same_x"] else p]
             want_x[o: o + rx[p - 1].size] += rx[p - 1]
     if not cplx:
         want_h, want_x = want_h.real, want_x.real
-    assert rel(gh, want_h) <= 20 * tol, (idx, c, "grad_h")
+    eh = rel(gh, want_h)
+    assert eh <= tol, (idx, c, "grad_h", eh)
     # x_1 receives no gradient from y (it enters only alpha)
-    assert rel(gx, want_x) <= 20 * tol, (idx, c, "grad_x")
+    ex = rel(gx, want_x)
+    assert ex <= tol, (idx, c, "grad_x", ex)
     plan.close()

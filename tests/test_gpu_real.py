@@ -84,7 +84,7 @@ def test_vandermonde_fp64_closed_form(dev):
     s = np.sum(a ** np.arange(n) * x)
     ref = s ** (m - 1) * a ** np.arange(n)
     assert rel_err(y[:n], ref) <= TOL64
-    assert abs(al[0] - s ** m) <= TOL64 * abs(s ** m) * 10
+    assert abs(al[0] - s ** m) <= TOL64 * abs(s ** m), (al[0], s ** m)
 
 
 @pytest.mark.parametrize("flags", [hk.SAME_X, hk.SAME_X | hk.ONE_PER_LAUNCH])
@@ -139,12 +139,12 @@ def test_fp64_batched_and_one_per_launch(dev):
 def test_edge_cases(dev, case):
     orders, dims = case
     rng = np.random.default_rng(sum(dims))
-    hs = [rng.standard_normal(m * (n - 1) + 1) for m, n in zip(orders, dims)]
-    xs = [rng.standard_normal(n) for n in dims]
+    hs = [rng.standard_normal(m * (n - 1) + 1) / np.sqrt(m * (n - 1) + 1) for m, n in zip(orders, dims)]
+    xs = [v / np.linalg.norm(v) for v in (rng.standard_normal(n) for n in dims)]
     b = wl.pack_square(orders, dims, hs, xs)
     for dtype, tol in [(hk.R32, TOL32), (hk.R64, TOL64)]:
         (y, a), _ = run(b, dtype, want_alpha=True, dev=dev)
-        check_batch(b, y, a, tol * (10 if max(orders) >= 8 else 1))
+        check_batch(b, y, a, tol)
 
 
 def test_longest_single_transform_fp32(dev):
@@ -177,12 +177,14 @@ def test_host_buffers_entry_point(dev):
     plan.close()
 
 
-def test_full_size_batch_sampled(dev):
+def test_full_size_batch_every_tensor(dev):
     # the 8192-tensor workload in the launch configuration the benchmark
-    # times; sampled outputs checked against the oracle one by one
+    # times, every output checked against the oracle (in a process pool)
+    from oracle import pool
     b = wl.batched_square(count=8192, seed=1)
     (y, _), info = run(b, hk.R32, dev=dev)
-    idx = np.random.default_rng(0).choice(len(b), size=48, replace=False)
-    idx = np.concatenate([idx, np.argsort(b.dims)[-4:], np.argsort(b.dims)[:4]])
-    check_batch(b, y, None, TOL32, idx=idx)
+    refs = pool.square_refs(b.tensor(i) for i in range(len(b)))
+    err = pool.relative_errors(b, y, refs)
+    print("8192 tensors: max rel err %.2e, median %.2e" % (err.max(), np.median(err)))
+    assert err.max() <= TOL32, (int(np.argmax(err)), err.max())
     assert info["count"] == 8192

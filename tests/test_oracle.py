@@ -276,3 +276,15 @@ def test_planted_mistakes_are_caught():
     }
     for name, y in wrong.items():
         assert np.max(np.abs(y - ref)) > 1e-3 * np.max(np.abs(ref)), name
+
+
+def test_pool_matches_serial_oracle():
+    # the process-pool helper the full-batch parity checks use returns the
+    # serial oracle's outputs, in order
+    from oracle import pool
+    from paper_1401_6238_gb300 import workloads as wl
+    b = wl.batched_square(count=9, seed=3, n_lo=16, n_hi=80)
+    tensors = [b.tensor(i) for i in range(len(b))]
+    par = pool.square_refs(tensors, procs=2)
+    for (m, n, h, x), y in zip(tensors, par):
+        np.testing.assert_array_equal(y, oracle.fast_y(h, [x] * (m - 1), [n] * m).real)

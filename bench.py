@@ -16,6 +16,9 @@ Reported (one JSON line on rank 0):
   fp64_plain   the plain FP64 path, one tensor per kernel launch, and the
                FP32/FP64 output agreement
   cpu_baseline the FP64 oracle on the host cores over a bounded sample
+  accuracy     per-tensor relative infinity-norm error of the timed FP32
+               output against the FP64 oracle, over every tensor of the batch
+               (max and median)
 --impl reference times the FP64 oracle alone (the CPU arm).
 """
 
@@ -33,9 +36,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "H·x^{m-1} products/s and % HBM roofline, batched FP32 vs plain FP64, same error"
-WORKLOAD = {"workload": "batched square real Hankel tensors, FP32",
+WORKLOAD = {"workload": "batched square real Hankel tensors",
             "tensors": 8192, "orders": [3, 4, 5], "n_range": [16, 1024],
             "h": "N(0,1/d)", "x": "unit-norm Gaussian", "product": "y = H x^{m-1}"}
+
+
+def bench_config(batch, copies):
+    """The workload's description, printed by both arms."""
+    return dict(WORKLOAD, l2="each step reads one of %d input copies (%.0f MB together, > 4x L2)"
+                % (copies, copies * (batch.h.nbytes + batch.x.nbytes) / 2e6),
+                parallelism="replicas: each rank its own 8192-tensor batch")
 
 
 def peaks():
@@ -61,6 +71,33 @@ def oracle_sample_worker(args):
         m, n, h, x = b.tensor(i)
         oracle.fast_y(h, [x] * (m - 1), [n] * m)
     return hi - lo
+
+
+def oracle_refs_worker(args):
+    """Oracle outputs y (FP64) of tensors lo .. hi-1 of the seeded batch."""
+    lo, hi, seed = args
+    import oracle
+    from paper_1401_6238_gb300 import workloads as wl
+    if seed not in _BATCH:
+        _BATCH[seed] = wl.batched_square(count=8192, seed=seed)
+    b = _BATCH[seed]
+    out = []
+    for i in range(lo, hi):
+        m, n, h, x = b.tensor(i)
+        out.append(oracle.fast_y(h, [x] * (m - 1), [n] * m).real)
+    return out
+
+
+def oracle_errors(batch, y, seed, pool):
+    """Per-tensor ||y_i - y_i^oracle||_inf / ||y_i^oracle||_inf over the batch."""
+    chunk = 64
+    tasks = [(lo, min(len(batch), lo + chunk), seed) for lo in range(0, len(batch), chunk)]
+    refs = [r for part in pool.map(oracle_refs_worker, tasks) for r in part]
+    err = np.empty(len(batch))
+    for i, ref in enumerate(refs):
+        o, n = batch.y_off[i], batch.dims[i]
+        err[i] = np.max(np.abs(y[o:o + n] - ref)) / np.max(np.abs(ref))
+    return err
 
 
 def cpu_oracle(seconds=12.0, seed=1, pool=None, cores=1):
@@ -153,7 +190,7 @@ def profiled_traffic():
     """DRAM bytes per step of the forward kernel from the committed ncu
     capture, or None when the kernel sources changed since it was taken."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "real_fwd_traffic.json")
+    path = os.path.join(ROOT, "profiles", "fast_fwd_traffic.json")
     try:
         with open(path) as fh:
             rec = json.load(fh)
@@ -166,19 +203,22 @@ def profiled_traffic():
         return None
 
 
-FP32_LANES_PER_SM, SMS = 128, 152
+FP32_LANES_PER_SM = 128
 # untimed run of the step under the clock sampler before the timed region
 SOAK_SECONDS = 0.8
 
 
-def alu_roofline(flops, kernel_ms, clocks):
+def alu_roofline(flops, kernel_ms, clocks, sms):
     """FP32 CUDA-core roofline of the forward step (flops per step / kernel
-    time against 2 x lanes x SMs x the median sampled SM clock)."""
+    time against 2 x lanes x SMs x the median sampled SM clock); ``sms`` is
+    the device's multiprocessor count."""
     mhz = (clocks or {}).get("sm_mhz") or 2070.0
-    peak = 2.0 * FP32_LANES_PER_SM * SMS * mhz * 1e6 / 1e12
+    peak = 2.0 * FP32_LANES_PER_SM * sms * mhz * 1e6 / 1e12
     achieved = flops / (kernel_ms / 1000.0) / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "flops_per_step": flops, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % mhz}
+            "flops_per_step": flops,
+            "peak_source": "derived: %d SMs (device multiprocessor count) x 128 FP32 lanes x 2 x %.0f MHz "
+                           "(median sampled SM clock)" % (sms, mhz)}
 
 
 def timed(fn, steps, warmup, stream):
@@ -439,6 +479,7 @@ def run_reference(args):
     if rank != 0:
         return
     import multiprocessing as mp
+    from paper_1401_6238_gb300 import workloads as wl
     cores = os.cpu_count() or 1
     ctx = mp.get_context("spawn")
     with ctx.Pool(cores) as pool:
@@ -455,7 +496,7 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": "products/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": dict(WORKLOAD),
+            "config": bench_config(wl.batched_square(count=8192, seed=rank_seed(0)), max(2, args.copies)),
             "cpu_baseline": {"value": value, "unit": "products/s", "cores": cores, "kind": "oracle",
                              "sample": "%d tensors of the 8192-tensor workload (FP64 radix-2 embedding FFT, "
                                        "spawn pool of %d processes), %d steps" % (total_n, cores, args.steps)},
@@ -655,26 +696,35 @@ def main():
     if not args.no_secondary and rank == 0:
         secondary = secondary_workloads(dev, stream)
 
-    cpu = None
+    cpu, accuracy = None, None
     if pool is not None:
         v, n, dt = cpu_oracle(seconds=15.0, pool=pool, cores=cores)
         cpu = {"value": v, "unit": "products/s", "cores": cores, "kind": "oracle",
                "sample": "first %d tensors of the same 8192-tensor batch, FP64 radix-2 embedding FFT, "
                          "spawn pool of %d processes, %.1f s" % (n, cores, dt)}
+        # the timed step's output against the oracle, every tensor
+        y_last = Ys[(args.warmup + args.steps - 1) % copies].double().cpu().numpy()
+        t0 = time.perf_counter()
+        err = oracle_errors(batch, y_last, rank_seed(rank), pool)
+        accuracy = {"max_rel_err": float(err.max()), "median_rel_err": float(np.median(err)),
+                    "tensors": int(err.size), "norm": "per-tensor relative infinity norm",
+                    "against": "FP64 oracle (radix-2 embedding at a power-of-two length)",
+                    "oracle_seconds": time.perf_counter() - t0}
         pool.close()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "products/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": dict(WORKLOAD, l2="each step reads one of %d input copies (%.0f MB together, "
-                                            "> 4x L2)" % (copies, copies * (batch.h.nbytes + batch.x.nbytes) / 2e6),
-                               parallelism="replicas: each rank its own 8192-tensor batch"),
+                "config": bench_config(batch, copies),
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": traffic,
-                             "peak_source": peak_src, "kernel": "real_fwd_kernel<float>",
+                             "peak_source": peak_src, "kernel": "fast_fwd_kernel<false>",
+                             "launches_per_step": int(info["launches"]),
                              "algorithmic_bytes_per_step": alg_bytes},
-                "roofline_alu": alu_roofline(alg_flops, kernel_ms, clocks),
+                "roofline_alu": alu_roofline(alg_flops, kernel_ms, clocks,
+                                             torch.cuda.get_device_properties(dev).multi_processor_count),
+                "accuracy": accuracy,
                 "e2e": e2e, "gpu_launches": int(info["launches"]) * args.steps,
                 "plan": info, "fp64_plain": fp64, "cpu_baseline": cpu, "clocks": clocks,
                 "secondary": secondary, "graph_replay": graph,

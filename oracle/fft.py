@@ -9,8 +9,8 @@ power-of-two length L >= d, deliberately a different length and a different
 algorithm from the CUDA path's mixed-radix Stockham transform.  The transform
 is iterative decimation in time: bit-reversal permutation, then log2(L)
 butterfly stages; the stage twiddles are numpy's FP64 ``exp``.
-Parity: pinned against ``numpy.fft.fft`` and an O(L^2) DFT in
-``tests/test_oracle_fft.py``.
+Parity: pinned against ``numpy.fft.fft`` and the O(L^2) Fourier-matrix
+product in ``tests/test_oracle.py`` (the FFT tests at its top).
 """
 
 import numpy as np

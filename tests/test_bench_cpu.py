@@ -49,14 +49,18 @@ def test_read_clocks_without_sampler_or_samples(tmp_path):
 
 
 def test_alu_roofline_arithmetic():
-    r = bench.alu_roofline(flops=1.0e9, kernel_ms=0.5, clocks={"sm_mhz": 2000.0})
+    r = bench.alu_roofline(flops=1.0e9, kernel_ms=0.5, clocks={"sm_mhz": 2000.0}, sms=152)
     peak = 2 * 128 * 152 * 2000e6 / 1e12  # FMA lanes x SMs x clock, TFLOP/s
     assert r["peak"] == pytest.approx(peak)
     assert r["achieved"] == pytest.approx(2.0)  # 1 GFLOP in 0.5 ms
     assert r["frac"] == pytest.approx(2.0 / peak)
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert "152 SMs" in r["peak_source"]
     # no clock record: the maximum SM clock
-    assert bench.alu_roofline(1.0e9, 0.5, None)["peak"] == pytest.approx(2 * 128 * 152 * 2070e6 / 1e12)
+    assert bench.alu_roofline(1.0e9, 0.5, None, 152)["peak"] == pytest.approx(2 * 128 * 152 * 2070e6 / 1e12)
+    # the SM count is the device's, not a constant
+    r = bench.alu_roofline(1.0e9, 0.5, {"sm_mhz": 2000.0}, sms=148)
+    assert r["peak"] == pytest.approx(2 * 128 * 148 * 2000e6 / 1e12) and "148 SMs" in r["peak_source"]
 
 
 def test_peak_is_the_measured_copy_bandwidth():
@@ -70,20 +74,55 @@ def test_peak_is_the_measured_copy_bandwidth():
 
 
 def test_traffic_record_follows_the_sources(tmp_path, monkeypatch):
-    rec_path = os.path.join(bench.ROOT, "profiles", "real_fwd_traffic.json")
-    with open(rec_path) as f:
-        rec = json.load(f)
-    # a copy of the tree holding the recorded sources, one of them changed
+    import hashlib
+    # a tree with two kernel sources and a record taken on them
     root = tmp_path / "tree"
-    for rel in rec["sources"] + ["profiles/real_fwd_traffic.json"]:
-        dst = root / rel
-        dst.parent.mkdir(parents=True, exist_ok=True)
-        shutil.copy(os.path.join(bench.ROOT, rel), dst)
+    srcs = ["pkg/a.cu", "pkg/b.cuh"]
+    for rel, text in zip(srcs, ["// kernel\n", "// header\n"]):
+        (root / rel).parent.mkdir(parents=True, exist_ok=True)
+        (root / rel).write_text(text)
+    h = hashlib.sha256()
+    for rel in srcs:
+        h.update((root / rel).read_bytes())
+    (root / "profiles").mkdir()
+    rec = {"bytes_per_step": 123456, "sources": srcs, "sources_sha256": h.hexdigest()}
+    (root / "profiles" / "fast_fwd_traffic.json").write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "ROOT", str(root))
-    same = bench.profiled_traffic()
-    with open(root / rec["sources"][0], "a") as f:
-        f.write("\n// changed\n")
+    assert bench.profiled_traffic() == 123456
+    with open(root / srcs[1], "a") as f:
+        f.write("// changed\n")
     assert bench.profiled_traffic() is None
-    # the unchanged copy reports the recorded bytes when the record matches it
-    if same is not None:
-        assert same == rec["bytes_per_step"]
+    # no record at all
+    os.remove(root / "profiles" / "fast_fwd_traffic.json")
+    assert bench.profiled_traffic() is None
+
+
+def test_both_arms_print_one_config():
+    from paper_1401_6238_gb300 import workloads as wl
+    b = wl.batched_square(count=8192, seed=bench.rank_seed(0))
+    a, c = bench.bench_config(b, 6), bench.bench_config(wl.batched_square(count=8192, seed=bench.rank_seed(0)), 6)
+    assert a == c
+    assert "FP32" not in a["workload"] and "f64" not in json.dumps(a)  # dtype carries the precision
+
+
+class _SerialPool:
+    def map(self, fn, tasks):
+        return [fn(t) for t in tasks]
+
+
+def test_oracle_errors_over_a_batch():
+    import numpy as np
+    import oracle
+    from paper_1401_6238_gb300 import workloads as wl
+    full = wl.batched_square(count=8192, seed=1)
+    b = full.subset(np.arange(70))
+    y = np.zeros(b.y_len)
+    for i in range(len(b)):
+        m, n, h, x = b.tensor(i)
+        y[b.y_off[i]: b.y_off[i] + n] = oracle.fast_y(h, [x] * (m - 1), [n] * m).real
+    assert np.all(bench.oracle_errors(b, y, 1, _SerialPool()) == 0.0)
+    # a relative error planted in tensor 37 is reported there alone
+    o, n = b.y_off[37], b.dims[37]
+    y[o + n // 2] += 1e-4 * np.max(np.abs(y[o:o + n]))
+    e = bench.oracle_errors(b, y, 1, _SerialPool())
+    assert e[37] == pytest.approx(1e-4) and np.all(np.delete(e, 37) == 0.0)

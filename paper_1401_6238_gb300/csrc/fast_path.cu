@@ -1,10 +1,11 @@
 // fast_path.cu -- one persistent launch for batches of real square tensors
 // with one vector per tensor: y = H x^{m-1} and alpha = H x^m (Section 2.1
 // notation), by the embedding of Section 3 at FFT lengths L = R 2T with
-// R in {16, 12} (powers of two and three times powers of two, 32..4096).
+// R in {16, 12} (powers of two and three times powers of two, 32..4096) and
+// L = 5120 (R = 20, T = 256).
 //
 // Work unit: a pair job, two tensors A and B with one FFT length L, run by a
-// group of T = L / (2R) threads.  Per tensor the generating vector and the
+// group of T = L / R threads.  Per tensor the generating vector and the
 // vector share one complex transform, S = fft(h~ + i x~) (zero-padded on
 // load); bins k and L-k of S give
 //     H_k = (S_k + conj S_{L-k}) / 2,  X_k = -i (S_k - conj S_{L-k}) / 2,
@@ -27,14 +28,15 @@
 // with bin (NB - u) + (R-1-s) NB, so the unpacking, the spectrum power and
 // the packing of P_A + i P_B need no data from other threads, and the first
 // pass of the final transform (radix R, the same butterflies, no twiddles)
-// starts from these registers.  Butterfly NB - u needs twiddles
-// w_L^{r (NB-u)} = w_R^r conj(w_L^{r u}): the conjugates of its partner's,
-// with the w_R^r factor done as a rotation of the transform's outputs
-// (DFT_R(a_r w_R^r)[s] = DFT_R(a)[s+1]).
+// starts from these registers.
 //
 // All other passes go through two shared-memory buffers written alternately
-// (one barrier per pass).  Twiddles come from two FP32 tables rounded from
-// FP64 (w_4096^e and w_3072^e) read through the L1 cache.
+// (one barrier per pass).  Twiddles come from three FP32 tables rounded from
+// FP64 (w_4096^e, w_3072^e and w_5120^e) held in shared memory.  P_A waits
+// in a thread-private shared-memory slab while tensor B is transformed; at
+// L = 5120 the two exchange buffers take that room and the slab is a
+// per-block slice of global memory (written and read back by the same
+// thread, so it stays in L2).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -58,6 +60,8 @@ constexpr int STASH = 16;                   // complex slots per thread of the t
 // w_3072^e = A3[e >> 6] B3[e & 63] (the stage_twiddle_kernel layout: A then B)
 constexpr int TW2 = 4096 / 64 + 64;
 constexpr int TW3 = 3072 / 64 + 64;
+constexpr int TW5 = 5120 / 64 + 64;
+constexpr int LONG = 5120;  // the one length whose slab lives in global memory
 
 // padded shared-memory index: one slot every 16 elements (bank spread)
 __device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
@@ -65,7 +69,7 @@ __device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr bool pow2(int v) { return (v & (v - 1)) == 0; }
 // radix of the last pass; the thread group of a job has one thread per
 // last-pass butterfly
-__host__ __device__ constexpr int rlast(int L) { return pow2(L) ? 16 : 12; }
+__host__ __device__ constexpr int rlast(int L) { return pow2(L) ? 16 : (L % 5 == 0 ? 20 : 12); }
 __host__ __device__ constexpr int nthr(int L) { return L / rlast(L); }
 // radix of the power-of-two passes for Q = L / R: 16 first, then the rest
 __host__ __device__ constexpr int q0(int Q) { return Q >= 16 ? 16 : Q; }
@@ -78,17 +82,34 @@ extern __shared__ __align__(16) unsigned char fp_smem[];
 __device__ __forceinline__ double* sm_red() { return reinterpret_cast<double*>(fp_smem); }
 __device__ __forceinline__ cx<float>* sm_t2() { return reinterpret_cast<cx<float>*>(fp_smem + RED * sizeof(double)); }
 __device__ __forceinline__ cx<float>* sm_t3() { return sm_t2() + TW2; }
-__device__ __forceinline__ cx<float>* sm_buf(int i) { return sm_t3() + TW3 + i * BUF; }
+__device__ __forceinline__ cx<float>* sm_t5() { return sm_t3() + TW3; }
+__device__ __forceinline__ cx<float>* sm_buf(int i) { return sm_t5() + TW5 + i * BUF; }
+// exchange buffer i of length L: BUF apart, or the padded lengths of the
+// block's groups apart when that is longer (L = 5120, whose two buffers then
+// cover the slab's room)
+__host__ __device__ constexpr int sm_bufL_stride(int L) {
+    return (BLOCK / (L / rlast(L))) * (L + L / 16) > BUF ? (BLOCK / (L / rlast(L))) * (L + L / 16) : BUF;
+}
+__host__ __device__ constexpr int sm_bufL_span(int L) {
+    return sm_bufL_stride(L) + (BLOCK / (L / rlast(L))) * (L + L / 16);
+}
+template <int L>
+__device__ __forceinline__ cx<float>* sm_bufL(int i) {
+    return sm_buf(0) + i * sm_bufL_stride(L);
+}
 // thread-private slab: slot s of thread i at sm_stash()[s * BLOCK + i]
 __device__ __forceinline__ cx<float>* sm_stash() { return sm_buf(2); }
 
 struct Tw {
-    // w_M^e for M dividing 4096 (a power of two) or 3072
+    // w_M^e for M dividing 4096 (a power of two), 5120 (a multiple of 5) or 3072
     template <int M>
     __device__ __forceinline__ cx<float> get(int e) const {
         if constexpr (pow2(M)) {
             const int f = e * (4096 / M);
             return cmul(sm_t2()[f >> 6], sm_t2()[64 + (f & 63)]);
+        } else if constexpr (M % 5 == 0) {
+            const int f = e * (5120 / M);
+            return cmul(sm_t5()[f >> 6], sm_t5()[80 + (f & 63)]);
         } else {
             const int f = e * (3072 / M);
             return cmul(sm_t3()[f >> 6], sm_t3()[48 + (f & 63)]);
@@ -294,6 +315,7 @@ struct Params {
     float* y;
     float* alpha;
     int* ctr;
+    cx<float>* slab;  // L = 5120: R BLOCK complex values per block
     int nitems;
     int after;  // the item after the next one (claimed during the current item)
 };
@@ -309,16 +331,21 @@ __device__ __noinline__ int run_item(int first, int staged, int next) {
     constexpr int R = rlast(L), T = nthr(L), Q = L / R, GS = L + L / 16;
     constexpr int QA = q0(Q), QB = q1(Q);  // power-of-two passes (QB == 1: none)
     constexpr int H = (T < 32 ? T : 32) / 2;  // mirror partner: lane ^ H
+    static_assert(BLOCK % T == 0, "a block holds whole groups");
+    static_assert(L == LONG ? (sm_bufL_span(L) <= 2 * BUF + STASH * BLOCK)
+                            : (sm_bufL_span(L) <= 2 * BUF && R <= STASH),
+                  "the exchange buffers (and the shared-memory slab) fit the dynamic shared memory");
     const Params& c = fp_par;
     const Tw tw;
     const int g = threadIdx.x / T, t = threadIdx.x % T;
     const FastJob& J = c.jobs[first + g];
-    auto buf = [&](int i) { return sm_buf(i) + g * GS; };
+    auto buf = [&](int i) { return sm_bufL<L>(i) + g * GS; };
     const bool wa = c.alpha != nullptr;
     const int b = last_b<T>(t);
     const bool self0 = b == 0, selfh = b == T / 2;  // self-mirrored butterflies
     cx<float> v[R];
-    cx<float>* const st = sm_stash() + threadIdx.x;  // P_A, slot s at st[s * BLOCK]
+    // P_A, slot s at st[s * BLOCK]
+    cx<float>* const st = (L == LONG ? c.slab + (size_t)blockIdx.x * R * BLOCK : sm_stash()) + threadIdx.x;
     double aA = 0.0, aB = 0.0;
     int after = 0;
     if (threadIdx.x == 0) after = atomicAdd(c.ctr, 1) + (int)gridDim.x;  // stored at the end
@@ -436,11 +463,13 @@ __global__ void __launch_bounds__(BLOCK, HK_FAST_MIN_BLOCKS)
     fast_fwd_kernel(const FastItem* __restrict__ items, int nitems, const FastJob* __restrict__ jobs,
                     const float* __restrict__ h, const float* __restrict__ x, float* __restrict__ y,
                     float* __restrict__ alpha, const cx<float>* __restrict__ tw2, const cx<float>* __restrict__ tw3,
-                    int* ctr) {
+                    const cx<float>* __restrict__ tw5, cx<float>* slab, int* ctr) {
     cx<float>* t2 = sm_t2();
     cx<float>* t3 = sm_t3();
+    cx<float>* t5 = sm_t5();
     for (int i = threadIdx.x; i < TW2; i += BLOCK) t2[i] = ldg_cx(tw2 + i);
     for (int i = threadIdx.x; i < TW3; i += BLOCK) t3[i] = ldg_cx(tw3 + i);
+    for (int i = threadIdx.x; i < TW5; i += BLOCK) t5[i] = ldg_cx(tw5 + i);
     if (threadIdx.x == 0) {
         fp_par.items = items;
         fp_par.jobs = jobs;
@@ -449,6 +478,7 @@ __global__ void __launch_bounds__(BLOCK, HK_FAST_MIN_BLOCKS)
         fp_par.y = y;
         fp_par.alpha = alpha;
         fp_par.ctr = ctr;
+        fp_par.slab = slab;
         fp_par.nitems = nitems;
         // items: blockIdx.x first, then claimed from the counter; the claim
         // of the item after the next one overlaps the current item
@@ -461,6 +491,7 @@ __global__ void __launch_bounds__(BLOCK, HK_FAST_MIN_BLOCKS)
     while (it < nitems) {
         const FastItem I = items[it];
         switch (I.L) {
+            case 5120: staged = run_item<5120, F64>(I.first, staged, next); break;
             case 4096: staged = run_item<4096, F64>(I.first, staged, next); break;
             case 3072: staged = run_item<3072, F64>(I.first, staged, next); break;
             case 2048: staged = run_item<2048, F64>(I.first, staged, next); break;
@@ -502,14 +533,14 @@ __global__ void __launch_bounds__(BLOCK, HK_FAST_MIN_BLOCKS)
 
 bool fast_length_ok(int L) {
     switch (L) {
-        case 4096: case 3072: case 2048: case 1536: case 1024: case 768: case 512: case 384:
+        case 5120: case 4096: case 3072: case 2048: case 1536: case 1024: case 768: case 512: case 384:
         case 256: case 192: case 128: case 96: case 64: case 48: case 32: return true;
         default: return false;
     }
 }
 
 int fast_length(int64_t d) {
-    static const int lens[] = {32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048, 3072, 4096};
+    static const int lens[] = {32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048, 3072, 4096, 5120};
     for (int L : lens)
         if (L >= d) return L;
     return 0;
@@ -517,14 +548,17 @@ int fast_length(int64_t d) {
 
 int fast_jobs_per_item(int L) { return fp::BLOCK / fp::nthr(L); }
 
+size_t fast_slab_bytes(int L) { return L == fp::LONG ? (size_t)fp::rlast(L) * fp::BLOCK * sizeof(cx<float>) : 0; }
+
 size_t fast_smem_bytes() {
     return fp::RED * sizeof(double) +
-           ((size_t)fp::TW2 + fp::TW3 + 2 * (size_t)fp::BUF + (size_t)fp::STASH * fp::BLOCK) * sizeof(cx<float>);
+           ((size_t)fp::TW2 + fp::TW3 + fp::TW5 + 2 * (size_t)fp::BUF + (size_t)fp::STASH * fp::BLOCK) *
+               sizeof(cx<float>);
 }
 
 cudaError_t launch_fast_forward(const FastItem* items, int nitems, int grid, const FastJob* jobs, const void* h,
-                                const void* x, void* y, void* alpha, const void* t2, const void* t3, int* ctr,
-                                int flags, cudaStream_t st) {
+                                const void* x, void* y, void* alpha, const void* t2, const void* t3, const void* t5,
+                                void* slab, int* ctr, int flags, cudaStream_t st) {
     const size_t smem = fast_smem_bytes();
     const bool f64 = (flags & HANKEL_FP64_POWER) != 0;
     auto k = f64 ? fp::fast_fwd_kernel<true> : fp::fast_fwd_kernel<false>;
@@ -551,7 +585,8 @@ cudaError_t launch_fast_forward(const FastItem* items, int nitems, int grid, con
         }
     }
     k<<<grid, fp::BLOCK, smem, st>>>(items, nitems, jobs, (const float*)h, (const float*)x, (float*)y, (float*)alpha,
-                                     (const cx<float>*)t2, (const cx<float>*)t3, ctr);
+                                     (const cx<float>*)t2, (const cx<float>*)t3, (const cx<float>*)t5,
+                                     (cx<float>*)slab, ctr);
     return cudaGetLastError();
 }
 

@@ -257,6 +257,8 @@ struct DFTpfa {
 };
 template <typename T>
 struct DFT<T, 12> : DFTpfa<T, 4, 3> {};
+template <typename T>
+struct DFT<T, 20> : DFTpfa<T, 4, 5> {};
 
 // ------------------------------------------------------------- shared memory
 // One padding slot every 16 elements spreads strided butterfly accesses over

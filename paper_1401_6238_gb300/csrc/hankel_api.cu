@@ -197,8 +197,10 @@ struct hankel_plan_s {
     hk::FastJob* d_fast_jobs = nullptr;
     hk::FastItem* d_fast_items = nullptr;
     int* d_fast_ctr = nullptr;
-    void* d_fast_tw = nullptr;  // two-level tables of w_4096 and w_3072 (FP32 complex)
+    void* d_fast_tw = nullptr;  // two-level tables of w_4096, w_3072 and w_5120 (FP32 complex)
     size_t fast_tw3 = 0;        // byte offset of the w_3072 table
+    size_t fast_tw5 = 0;        // byte offset of the w_5120 table
+    void* d_fast_slab = nullptr;  // per-block slab of the longest length (or null)
     int fast_grid = 0;
     int64_t fast_pairs = 0;  // pair jobs with at least one tensor (the rest pad items)
     // general path (complex data, distinct vectors, BHHB)
@@ -254,6 +256,7 @@ void free_plan(hankel_plan_s* p) {
     cudaFree(p->d_fast_items);
     cudaFree(p->d_fast_ctr);
     cudaFree(p->d_fast_tw);
+    cudaFree(p->d_fast_slab);
     cudaFree(p->d_multi);
     cudaFree(p->d_tw);
     cudaFree(p->d_ws);
@@ -490,15 +493,22 @@ hankel_status build_fast(hankel_plan_s* p, const std::vector<char>& sel) {
     if ((e = cudaMalloc(&p->d_fast_items, p->fast_items.size() * sizeof(hk::FastItem))) != cudaSuccess)
         return cuda_fail(e, "cudaMalloc(jobs)");
     if ((e = cudaMalloc(&p->d_fast_ctr, 2 * sizeof(int))) != cudaSuccess) return cuda_fail(e, "cudaMalloc(counter)");
-    hk::FftPlan P2, P3;
+    // items are longest first: the first one's length sizes the slab
+    const size_t slab = hk::fast_slab_bytes(p->fast_items.front().L);
+    if (slab > 0 && (e = cudaMalloc(&p->d_fast_slab, slab * p->fast_grid)) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc(slab)");
+    hk::FftPlan P2, P3, P5;
     std::memset(&P2, 0, sizeof(P2));
     std::memset(&P3, 0, sizeof(P3));
+    std::memset(&P5, 0, sizeof(P5));
     P2.L = 4096;
     P3.L = 3072;
-    const int n2 = hk::stage_twiddle_count(P2), n3 = hk::stage_twiddle_count(P3);
-    if ((e = cudaMalloc(&p->d_fast_tw, (size_t)(n2 + n3) * 2 * sizeof(float))) != cudaSuccess)
+    P5.L = 5120;
+    const int n2 = hk::stage_twiddle_count(P2), n3 = hk::stage_twiddle_count(P3), n5 = hk::stage_twiddle_count(P5);
+    if ((e = cudaMalloc(&p->d_fast_tw, (size_t)(n2 + n3 + n5) * 2 * sizeof(float))) != cudaSuccess)
         return cuda_fail(e, "cudaMalloc(twiddles)");
     p->fast_tw3 = (size_t)n2 * 2 * sizeof(float);
+    p->fast_tw5 = (size_t)(n2 + n3) * 2 * sizeof(float);
     e = cudaMemcpy(p->d_fast_jobs, p->fast_jobs.data(), p->fast_jobs.size() * sizeof(hk::FastJob),
                    cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -507,6 +517,7 @@ hankel_status build_fast(hankel_plan_s* p, const std::vector<char>& sel) {
     if (e == cudaSuccess) e = cudaMemset(p->d_fast_ctr, 0, 2 * sizeof(int));
     if (e == cudaSuccess) e = hk::launch_stage_twiddles(false, p->d_fast_tw, P2, 0);
     if (e == cudaSuccess) e = hk::launch_stage_twiddles(false, (char*)p->d_fast_tw + p->fast_tw3, P3, 0);
+    if (e == cudaSuccess) e = hk::launch_stage_twiddles(false, (char*)p->d_fast_tw + p->fast_tw5, P5, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "fast path set-up");
     p->fast = true;
@@ -1194,7 +1205,8 @@ hankel_status hankel_txv(hankel_plan_t p, const void* h, const void* x, void* y,
     auto fast = [&](cudaStream_t s) {
         const char* t2 = (const char*)p->d_fast_tw;
         return hk::launch_fast_forward(p->d_fast_items, (int)p->fast_items.size(), p->fast_grid, p->d_fast_jobs, h, x,
-                                       y, alpha, t2, t2 + p->fast_tw3, p->d_fast_ctr, (int)p->flags, s);
+                                       y, alpha, t2, t2 + p->fast_tw3, t2 + p->fast_tw5, p->d_fast_slab,
+                                       p->d_fast_ctr, (int)p->flags, s);
     };
     cudaError_t e;
     if (p->fwd_launches.empty() || p->streams.empty()) {

@@ -34,15 +34,18 @@ cudaError_t launch_fold(bool dbl, bool cplx, const ExpandEntry* e, const FoldGro
 cudaError_t launch_stage_twiddles(bool dbl, void* out, const FftPlan& P, cudaStream_t st);
 int stage_twiddle_count(const FftPlan& P);
 // persistent forward kernel of fast_path.cu: its FFT lengths, jobs per item
-// and launch (t2 = w_4096^e, t3 = w_3072^e tables; ctr = two zeroed ints)
+// and launch (t2, t3, t5 = the w_4096^e, w_3072^e, w_5120^e tables; slab =
+// grid x fast_slab_bytes(L) bytes for the longest length L of the items;
+// ctr = two zeroed ints)
 bool fast_length_ok(int L);
 int fast_length(int64_t d);
 int fast_jobs_per_item(int L);
 int fast_blocks_per_sm();
 size_t fast_smem_bytes();
+size_t fast_slab_bytes(int L);
 cudaError_t launch_fast_forward(const FastItem* items, int nitems, int grid, const FastJob* jobs, const void* h,
-                                const void* x, void* y, void* alpha, const void* t2, const void* t3, int* ctr,
-                                int flags, cudaStream_t st);
+                                const void* x, void* y, void* alpha, const void* t2, const void* t3, const void* t5,
+                                void* slab, int* ctr, int flags, cudaStream_t st);
 size_t real_launch_smem(bool dbl, const RealLaunch& lc);
 bool fft_factor(int L, FftPlan* P);
 void set_last_error(const std::string& msg);

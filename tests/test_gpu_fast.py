@@ -3,8 +3,8 @@ one vector per tensor, y = H x^{m-1} and alpha = H x^m, Section 3) against
 the FP64 oracle, through the C ABI.
 
 The kernel runs every tensor whose generating length d fits one of its FFT
-lengths (2^k and 3 * 2^k, 32..4096); longer ones run on the per-length
-launches in the same call.  Inputs use the benchmark's scaling (h ~ N(0, 1/d),
+lengths (2^k and 3 * 2^k, 32..4096, and 5120); longer ones run on the
+per-length launches in the same call.  Inputs use the benchmark's scaling (h ~ N(0, 1/d),
 unit-norm x), at which the FP32 bound is 1e-5 relative in the infinity norm
 for every order tested here.
 """
@@ -20,7 +20,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL32 = 1e-5
-FAST_LENGTHS = [32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048, 3072, 4096]
+FAST_LENGTHS = [32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048, 3072, 4096, 5120]
 
 
 @pytest.fixture(scope="module")
@@ -141,11 +141,12 @@ def test_y_only_and_alpha_only(dev):
 
 
 def test_mixed_with_longer_lengths(dev):
-    # generating lengths above 4096 run on the per-length launches of the
+    # generating lengths above 5120 run on the per-length launches of the
     # same call; both sets must be right, and the plan reports both launches
-    shapes = [(5, 1000), (5, 1024), (4, 1300), (3, 2000), (5, 900), (3, 700), (4, 300), (3, 40)]
+    shapes = [(5, 1000), (5, 1024), (4, 1300), (3, 2000), (5, 900), (3, 700), (4, 300), (3, 40), (2, 2561)]
     b = scaled_tensors(shapes, seed=9)
-    (y, a) = run(b, dev=dev)[0][0]
+    (y, a), info = (lambda o: (o[0][0], o[1]))(run(b, dev=dev))
+    assert info["launches"] > 1
     check(b, y, a)
 
 
@@ -160,11 +161,23 @@ def test_repeat_calls_identical(dev):
 
 
 def test_benchmark_shapes_one_launch(dev):
-    # the benchmark's shape mix restricted to generating lengths <= 4096
-    # (orders 3 and 4): a single persistent launch
-    b = wl.batched_square(count=512, seed=36, orders=(3, 4), n_lo=16, n_hi=1024)
+    # the benchmark's shape mix (orders 3..5, n in [16, 1024], so d <= 5116):
+    # a single persistent launch
+    b = wl.batched_square(count=512, seed=36, orders=(3, 4, 5), n_lo=16, n_hi=1024)
+    assert max(m * (n - 1) + 1 for m, n in zip(b.orders, b.dims)) > 4096  # the longest length is in it
     outs, info = run(b, dev=dev)
     assert info["launches"] == 1
+    check(b, outs[0][0], outs[0][1])
+
+
+def test_longest_length_items_share_the_slab(dev):
+    # many tensors of FFT length 5120 (one job per block, the slab in global
+    # memory): more jobs than resident blocks, so blocks reuse their slab
+    shapes = [(5, 821 + (i * 37) % 204) for i in range(700)]
+    b = scaled_tensors(shapes, seed=38)
+    outs, info = run(b, dev=dev, calls=2)
+    assert info["launches"] == 1
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
     check(b, outs[0][0], outs[0][1])
 
 

@@ -1,6 +1,9 @@
-"""hankel_txv inside a CUDA graph: the forked launches (plan streams joined
-back with events) are captured once and replayed; replays on new inputs
-give the same results as direct calls."""
+"""hankel_txv inside a CUDA graph, captured once and replayed: the benchmark's
+shape mix as its one persistent launch (whose work counter re-arms itself
+at the end of every launch), and a batch with tensors longer than the
+persistent kernel's lengths, whose extra launches fork over the plan's
+streams and join back with events.  Replays on new inputs give the same
+bits as direct calls."""
 
 import numpy as np
 import pytest
@@ -20,10 +23,13 @@ def dev():
     return torch.device("cuda:0")
 
 
-def test_capture_and_replay(dev):
-    b = wl.batched_square(count=300, seed=17, n_lo=16, n_hi=1024)
+@pytest.mark.parametrize("n_hi,launches", [(1024, 1), (2000, 2)])
+def test_capture_and_replay(dev, n_hi, launches):
+    # n <= 1024, m <= 5: d <= 5116, one persistent launch; n up to 2000
+    # reaches d > 5120, which adds the per-length launches
+    b = wl.batched_square(count=300, seed=17, n_lo=16, n_hi=n_hi)
     plan = hk.Plan(hk.batch_descs(b), hk.R32, hk.SAME_X)
-    assert plan.info["launches"] > 1  # the fork/join path is what gets captured
+    assert (plan.info["launches"] == 1) if launches == 1 else (plan.info["launches"] > 1)
     H = torch.tensor(b.h, dtype=torch.float32, device=dev)
     X = torch.tensor(b.x, dtype=torch.float32, device=dev)
     Y = torch.zeros(b.y_len, dtype=torch.float32, device=dev)
@@ -38,7 +44,7 @@ def test_capture_and_replay(dev):
     with torch.cuda.graph(g):
         plan.txv(H, X, Y, A)
     for seed in (18, 19):
-        b2 = wl.batched_square(count=300, seed=17, n_lo=16, n_hi=1024)
+        b2 = wl.batched_square(count=300, seed=17, n_lo=16, n_hi=n_hi)
         rng = np.random.default_rng(seed)
         H.copy_(torch.tensor(b2.h * rng.uniform(0.5, 2.0), dtype=torch.float32))
         X.copy_(torch.tensor(b2.x, dtype=torch.float32))

@@ -41,6 +41,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "fft_core.cuh"
 #include "launch.h"
@@ -248,9 +249,11 @@ __device__ __forceinline__ void last_pass(cx<float>* v, const cx<float>* src, in
 
 // Spectral product at bin k: S_k = a, S_{L-k} = c; returns
 // P_k = conj(H_k)/L X_k^{m-1} (H, X unpacked from S, e = m - 1, sc = 2^-m / L)
-// and adds Re(P_k X_k) to acc when alpha is wanted.
-template <bool F64>
-__device__ __forceinline__ cx<float> product(cx<float> a, cx<float> c, int e, float sc, bool wa, double& acc) {
+// and, when alpha is wanted (WA), adds Re(P_k X_k) to acc.  The FP32 path
+// sums alpha in FP32 throughout (its terms carry FP32 rounding already):
+// an FP64 instruction holds this GPU's narrow FP64 pipe for many cycles.
+template <bool F64, bool WA, typename A>
+__device__ __forceinline__ cx<float> product(cx<float> a, cx<float> c, int e, float sc, A& acc) {
     if constexpr (F64) {
         const double hx = (double)a.x + c.x, hy = (double)a.y - c.y;
         const cx<double> X = mk<double>((double)a.y + c.y, (double)c.x - a.x);
@@ -261,7 +264,7 @@ __device__ __forceinline__ cx<float> product(cx<float> a, cx<float> c, int e, fl
             if (e & 2) p = cmul(p, X2);
             if (e & 4) p = cmul(p, cmul(X2, X2));
         }
-        if (wa) acc += 0.5 * (p.x * X.x - p.y * X.y);
+        if constexpr (WA) acc += 0.5 * (p.x * X.x - p.y * X.y);
         return mk<float>((float)p.x, (float)p.y);
     } else {
         const cx<float> X = mk<float>(a.y + c.y, c.x - a.x);
@@ -272,7 +275,7 @@ __device__ __forceinline__ cx<float> product(cx<float> a, cx<float> c, int e, fl
             if (e & 2) p = cmul(p, X2);
             if (e & 4) p = cmul(p, cmul(X2, X2));
         }
-        if (wa) acc += (double)(0.5f * (p.x * X.x - p.y * X.y));
+        if constexpr (WA) acc += 0.5f * (p.x * X.x - p.y * X.y);
         return p;
     }
 }
@@ -289,17 +292,19 @@ __device__ __forceinline__ void gsync(int g) {
     }
 }
 
-// Sum of one double over the T threads of a group (valid in thread 0 of the group).
-template <int T>
-__device__ __forceinline__ double group_sum(double v, double* red, int g, int t) {
+// Sum of one value over the T threads of a group (valid in thread 0 of the
+// group); the partial sums of the warps meet in the reduction scratch.
+template <int T, typename A>
+__device__ __forceinline__ A group_sum(A v, double* red, int g, int t) {
 #pragma unroll
     for (int o = (T < 32 ? T : 32) / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if constexpr (T > 32) {
-        if ((t & 31) == 0) red[g * (T / 32) + (t >> 5)] = v;
+        A* r = reinterpret_cast<A*>(red);
+        if ((t & 31) == 0) r[g * (T / 32) + (t >> 5)] = v;
         gsync<T>(g);
-        double s = 0.0;
+        A s = 0;
         if (t == 0)
-            for (int i = 0; i < T / 32; ++i) s += red[g * (T / 32) + i];
+            for (int i = 0; i < T / 32; ++i) s += r[g * (T / 32) + i];
         gsync<T>(g);
         return s;
     }
@@ -326,7 +331,7 @@ __shared__ Params fp_par;
 // this job's first input, or -1.  `next`: the index of the block's next
 // item; when it has the same length its first input is staged here, into
 // the buffer returned (-1 otherwise).
-template <int L, bool F64>
+template <int L, bool F64, bool WA>
 __device__ __noinline__ int run_item(int first, int staged, int next) {
     constexpr int R = rlast(L), T = nthr(L), Q = L / R, GS = L + L / 16;
     constexpr int QA = q0(Q), QB = q1(Q);  // power-of-two passes (QB == 1: none)
@@ -340,13 +345,13 @@ __device__ __noinline__ int run_item(int first, int staged, int next) {
     const int g = threadIdx.x / T, t = threadIdx.x % T;
     const FastJob& J = c.jobs[first + g];
     auto buf = [&](int i) { return sm_bufL<L>(i) + g * GS; };
-    const bool wa = c.alpha != nullptr;
+    using Acc = typename std::conditional<F64, double, float>::type;
     const int b = last_b<T>(t);
     const bool self0 = b == 0, selfh = b == T / 2;  // self-mirrored butterflies
     cx<float> v[R];
     // P_A, slot s at st[s * BLOCK]
     cx<float>* const st = (L == LONG ? c.slab + (size_t)blockIdx.x * R * BLOCK : sm_stash()) + threadIdx.x;
-    double aA = 0.0, aB = 0.0;
+    Acc aA = 0, aB = 0;
     int after = 0;
     if (threadIdx.x == 0) after = atomicAdd(c.ctr, 1) + (int)gridDim.x;  // stored at the end
 
@@ -378,13 +383,13 @@ __device__ __noinline__ int run_item(int first, int staged, int next) {
         // slot R-1-s, or this lane's own slot for the self-mirrored butterflies
         const float sc = ldexpf(1.0f / (float)L, -m);
         const int e = m - 1;
-        double a = 0.0;
+        Acc a = 0;
 #pragma unroll
         for (int s = 0; s < R; ++s) {
             const cx<float> o = v[R - 1 - s];
             cx<float> cpart = mk<float>(__shfl_xor_sync(0xffffffffu, o.x, H), __shfl_xor_sync(0xffffffffu, o.y, H));
             cpart = sel(self0, v[(R - s) % R], sel(selfh, o, cpart));
-            const cx<float> p = product<F64>(v[s], cpart, e, sc, wa, a);
+            const cx<float> p = product<F64, WA>(v[s], cpart, e, sc, a);
             // tensor A: P_A; tensor B: Q = P_A + i P_B (v still holds S_B)
             st[s * BLOCK] = B ? plus_i(st[s * BLOCK], p) : p;
         }
@@ -446,9 +451,9 @@ __device__ __noinline__ int run_item(int first, int staged, int next) {
             }
         }
     }
-    if (wa) {
-        const double sA = group_sum<T>(aA, sm_red(), g, t);
-        const double sB = group_sum<T>(aB, sm_red(), g, t);
+    if constexpr (WA) {
+        const Acc sA = group_sum<T>(aA, sm_red(), g, t);
+        const Acc sB = group_sum<T>(aB, sm_red(), g, t);
         if (t == 0) {
             if (J.iA >= 0) c.alpha[J.iA] = (float)sA;
             if (J.iB >= 0) c.alpha[J.iB] = (float)sB;
@@ -458,7 +463,7 @@ __device__ __noinline__ int run_item(int first, int staged, int next) {
     return staged_next;
 }
 
-template <bool F64>
+template <bool F64, bool WA>
 __global__ void __launch_bounds__(BLOCK, HK_FAST_MIN_BLOCKS)
     fast_fwd_kernel(const FastItem* __restrict__ items, int nitems, const FastJob* __restrict__ jobs,
                     const float* __restrict__ h, const float* __restrict__ x, float* __restrict__ y,
@@ -491,22 +496,22 @@ __global__ void __launch_bounds__(BLOCK, HK_FAST_MIN_BLOCKS)
     while (it < nitems) {
         const FastItem I = items[it];
         switch (I.L) {
-            case 5120: staged = run_item<5120, F64>(I.first, staged, next); break;
-            case 4096: staged = run_item<4096, F64>(I.first, staged, next); break;
-            case 3072: staged = run_item<3072, F64>(I.first, staged, next); break;
-            case 2048: staged = run_item<2048, F64>(I.first, staged, next); break;
-            case 1536: staged = run_item<1536, F64>(I.first, staged, next); break;
-            case 1024: staged = run_item<1024, F64>(I.first, staged, next); break;
-            case 768: staged = run_item<768, F64>(I.first, staged, next); break;
-            case 512: staged = run_item<512, F64>(I.first, staged, next); break;
-            case 384: staged = run_item<384, F64>(I.first, staged, next); break;
-            case 256: staged = run_item<256, F64>(I.first, staged, next); break;
-            case 192: staged = run_item<192, F64>(I.first, staged, next); break;
-            case 128: staged = run_item<128, F64>(I.first, staged, next); break;
-            case 96: staged = run_item<96, F64>(I.first, staged, next); break;
-            case 64: staged = run_item<64, F64>(I.first, staged, next); break;
-            case 48: staged = run_item<48, F64>(I.first, staged, next); break;
-            case 32: staged = run_item<32, F64>(I.first, staged, next); break;
+            case 5120: staged = run_item<5120, F64, WA>(I.first, staged, next); break;
+            case 4096: staged = run_item<4096, F64, WA>(I.first, staged, next); break;
+            case 3072: staged = run_item<3072, F64, WA>(I.first, staged, next); break;
+            case 2048: staged = run_item<2048, F64, WA>(I.first, staged, next); break;
+            case 1536: staged = run_item<1536, F64, WA>(I.first, staged, next); break;
+            case 1024: staged = run_item<1024, F64, WA>(I.first, staged, next); break;
+            case 768: staged = run_item<768, F64, WA>(I.first, staged, next); break;
+            case 512: staged = run_item<512, F64, WA>(I.first, staged, next); break;
+            case 384: staged = run_item<384, F64, WA>(I.first, staged, next); break;
+            case 256: staged = run_item<256, F64, WA>(I.first, staged, next); break;
+            case 192: staged = run_item<192, F64, WA>(I.first, staged, next); break;
+            case 128: staged = run_item<128, F64, WA>(I.first, staged, next); break;
+            case 96: staged = run_item<96, F64, WA>(I.first, staged, next); break;
+            case 64: staged = run_item<64, F64, WA>(I.first, staged, next); break;
+            case 48: staged = run_item<48, F64, WA>(I.first, staged, next); break;
+            case 32: staged = run_item<32, F64, WA>(I.first, staged, next); break;
             default: staged = -1; break;
         }
         // the staged copies must land before the next item reads them
@@ -560,16 +565,18 @@ cudaError_t launch_fast_forward(const FastItem* items, int nitems, int grid, con
                                 const void* x, void* y, void* alpha, const void* t2, const void* t3, const void* t5,
                                 void* slab, int* ctr, int flags, cudaStream_t st) {
     const size_t smem = fast_smem_bytes();
-    const bool f64 = (flags & HANKEL_FP64_POWER) != 0;
-    auto k = f64 ? fp::fast_fwd_kernel<true> : fp::fast_fwd_kernel<false>;
+    const bool f64 = (flags & HANKEL_FP64_POWER) != 0, wa = alpha != nullptr;
+    auto k = f64 ? (wa ? fp::fast_fwd_kernel<true, true> : fp::fast_fwd_kernel<true, false>)
+                 : (wa ? fp::fast_fwd_kernel<false, true> : fp::fast_fwd_kernel<false, false>);
+    const int variant = 2 * f64 + wa;
     static std::mutex mu;
-    static bool done[2][64] = {};
+    static bool done[4][64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     {
         std::lock_guard<std::mutex> lk(mu);
-        if (dev < 64 && !done[f64][dev]) {
+        if (dev < 64 && !done[variant][dev]) {
             e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             // shared memory for the resident blocks only; the rest stays L1
             // (spill slots, descriptors)
@@ -581,7 +588,7 @@ cudaError_t launch_fast_forward(const FastItem* items, int nitems, int grid, con
                 e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
             }
             if (e != cudaSuccess) return e;
-            done[f64][dev] = true;
+            done[variant][dev] = true;
         }
     }
     k<<<grid, fp::BLOCK, smem, st>>>(items, nitems, jobs, (const float*)h, (const float*)x, (float*)y, (float*)alpha,

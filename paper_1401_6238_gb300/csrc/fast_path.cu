@@ -247,36 +247,70 @@ __device__ __forceinline__ void last_pass(cx<float>* v, const cx<float>* src, in
 
 // ------------------------------------------------------------ the product
 
-// Spectral product at bin k: S_k = a, S_{L-k} = c; returns
-// P_k = conj(H_k)/L X_k^{m-1} (H, X unpacked from S, e = m - 1, sc = 2^-m / L)
-// and, when alpha is wanted (WA), adds Re(P_k X_k) to acc.  The FP32 path
-// sums alpha in FP32 throughout (its terms carry FP32 rounding already):
-// an FP64 instruction holds this GPU's narrow FP64 pipe for many cycles.
-template <bool F64, bool WA, typename A>
-__device__ __forceinline__ cx<float> product(cx<float> a, cx<float> c, int e, float sc, A& acc) {
-    if constexpr (F64) {
-        const double hx = (double)a.x + c.x, hy = (double)a.y - c.y;
-        const cx<double> X = mk<double>((double)a.y + c.y, (double)c.x - a.x);
-        cx<double> p = mk<double>(hx * sc, -hy * sc);
+// X^E for E = 1 .. 4 with the fewest dependent products; E = 0 takes the
+// exponent e (1 .. 7) at run time.
+template <int E, typename C>
+__device__ __forceinline__ C times_pow(C p, C X, int e) {
+    if constexpr (E == 1) {
+        return cmul(p, X);
+    } else if constexpr (E == 2) {
+        return cmul(p, cmul(X, X));
+    } else if constexpr (E == 3) {
+        return cmul(cmul(p, X), cmul(X, X));
+    } else if constexpr (E == 4) {
+        const C X2 = cmul(X, X);
+        return cmul(p, cmul(X2, X2));
+    } else {
         if (e & 1) p = cmul(p, X);
         if (e & 6) {
-            const cx<double> X2 = cmul(X, X);
+            const C X2 = cmul(X, X);
             if (e & 2) p = cmul(p, X2);
             if (e & 4) p = cmul(p, cmul(X2, X2));
         }
+        return p;
+    }
+}
+
+// Spectral product at bin k without its scale: S_k = a, S_{L-k} = c;
+// returns conj(2 H_k) (2 X_k)^e with H, X unpacked from S (e = m - 1), which
+// is 2^m L P_k for P_k = conj(H_k)/L X_k^{m-1}; the power-of-two factor
+// 2^-m / L is applied, exactly, to y and alpha on store.  When alpha is
+// wanted (WA), adds Re(2^m L P_k 2 X_k) / 2 to acc.  The FP32 path sums alpha
+// in FP32 throughout (its terms carry FP32 rounding already): an FP64
+// instruction holds this GPU's narrow FP64 pipe for many cycles.
+template <bool F64, bool WA, int E, typename A>
+__device__ __forceinline__ cx<float> product(cx<float> a, cx<float> c, int e, A& acc) {
+    if constexpr (F64) {
+        const cx<double> X = mk<double>((double)a.y + c.y, (double)c.x - a.x);
+        const cx<double> p = times_pow<E>(mk<double>((double)a.x + c.x, (double)c.y - a.y), X, e);
         if constexpr (WA) acc += 0.5 * (p.x * X.x - p.y * X.y);
         return mk<float>((float)p.x, (float)p.y);
     } else {
         const cx<float> X = mk<float>(a.y + c.y, c.x - a.x);
-        cx<float> p = mk<float>((a.x + c.x) * sc, (c.y - a.y) * sc);
-        if (e & 1) p = cmul(p, X);
-        if (e & 6) {
-            const cx<float> X2 = cmul(X, X);
-            if (e & 2) p = cmul(p, X2);
-            if (e & 4) p = cmul(p, cmul(X2, X2));
-        }
+        const cx<float> p = times_pow<E>(mk<float>(a.x + c.x, c.y - a.y), X, e);
         if constexpr (WA) acc += 0.5f * (p.x * X.x - p.y * X.y);
         return p;
+    }
+}
+
+// The spectral products of one tensor on the thread's bins b + s NB, s < R
+// (v: the spectrum S on those bins).  Bin b + s NB pairs with bin
+// L - (b + s NB): slot R-1-s of the mirror-partner lane (lane ^ H); the
+// lane of butterfly NB/2 is its own partner (it reads its own slot R-1-s by
+// shuffling from itself) and the lane of butterfly 0 pairs slot s with its
+// own slot (R-s) mod R, which is the previous step's slot R-1-s.
+// B == false: P_A into the slab; B == true: Q = P_A + i P_B into the slab.
+template <int R, bool F64, bool WA, int E, typename A>
+__device__ __forceinline__ void products(const cx<float>* v, cx<float>* st, bool B, int src, bool self0, int e, A& acc) {
+    cx<float> prev = v[0];
+#pragma unroll
+    for (int s = 0; s < R; ++s) {
+        const cx<float> o = v[R - 1 - s];
+        cx<float> cpart = mk<float>(__shfl_sync(0xffffffffu, o.x, src), __shfl_sync(0xffffffffu, o.y, src));
+        cpart = sel(self0, prev, cpart);
+        prev = o;
+        const cx<float> p = product<F64, WA, E>(v[s], cpart, e, acc);
+        st[s * BLOCK] = B ? plus_i(st[s * BLOCK], p) : p;
     }
 }
 
@@ -347,7 +381,8 @@ __device__ __noinline__ int run_item(int first, int staged, int next) {
     auto buf = [&](int i) { return sm_bufL<L>(i) + g * GS; };
     using Acc = typename std::conditional<F64, double, float>::type;
     const int b = last_b<T>(t);
-    const bool self0 = b == 0, selfh = b == T / 2;  // self-mirrored butterflies
+    const bool self0 = b == 0;  // self-mirrored butterflies 0 and T/2
+    const int lane = threadIdx.x & 31, src = (b == T / 2) ? lane : (lane ^ H);
     cx<float> v[R];
     // P_A, slot s at st[s * BLOCK]
     cx<float>* const st = (L == LONG ? c.slab + (size_t)blockIdx.x * R * BLOCK : sm_stash()) + threadIdx.x;
@@ -379,19 +414,18 @@ __device__ __noinline__ int run_item(int first, int staged, int next) {
         // the other buffer is free: tensor B's input streams in meanwhile
         if (!B) stage<L, T>(buf(cur ^ 1), c.h + J.hB, J.dB, c.x + J.xB, J.nB, t);
         last_pass<L, R>(v, buf(cur), b, tw);
-        // bin b + s NB pairs with bin L - (b + s NB): the partner lane's
-        // slot R-1-s, or this lane's own slot for the self-mirrored butterflies
-        const float sc = ldexpf(1.0f / (float)L, -m);
         const int e = m - 1;
         Acc a = 0;
-#pragma unroll
-        for (int s = 0; s < R; ++s) {
-            const cx<float> o = v[R - 1 - s];
-            cx<float> cpart = mk<float>(__shfl_xor_sync(0xffffffffu, o.x, H), __shfl_xor_sync(0xffffffffu, o.y, H));
-            cpart = sel(self0, v[(R - s) % R], sel(selfh, o, cpart));
-            const cx<float> p = product<F64, WA>(v[s], cpart, e, sc, a);
-            // tensor A: P_A; tensor B: Q = P_A + i P_B (v still holds S_B)
-            st[s * BLOCK] = B ? plus_i(st[s * BLOCK], p) : p;
+        if constexpr (T >= 32) {
+            // the power with a compile-time exponent for the common orders
+            switch (e) {
+                case 2: products<R, F64, WA, 2>(v, st, B, src, self0, e, a); break;
+                case 3: products<R, F64, WA, 3>(v, st, B, src, self0, e, a); break;
+                case 4: products<R, F64, WA, 4>(v, st, B, src, self0, e, a); break;
+                default: products<R, F64, WA, 0>(v, st, B, src, self0, e, a); break;
+            }
+        } else {
+            products<R, F64, WA, 0>(v, st, B, src, self0, e, a);
         }
         if (!B) {
             aA = a;
@@ -436,6 +470,7 @@ __device__ __noinline__ int run_item(int first, int staged, int next) {
         const int nA = J.nA, nB = J.nB, nmax = max(nA, nB);
         float* yA = c.y + J.yA;
         float* yB = c.y + J.yB;
+        const float scA = ldexpf(1.0f / (float)L, -J.mA), scB = ldexpf(1.0f / (float)L, -J.mB);
 #pragma unroll 1
         for (int j = 0; j < IT; ++j) {
             const int bl = t + T * j;
@@ -445,8 +480,8 @@ __device__ __noinline__ int run_item(int first, int staged, int next) {
 #pragma unroll
                 for (int s = 0; s < QA; ++s) {
                     const int i0 = bl + s * NBL;
-                    if (i0 < nA) yA[i0] = w[s].x;
-                    if (i0 < nB) yB[i0] = w[s].y;
+                    if (i0 < nA) yA[i0] = w[s].x * scA;
+                    if (i0 < nB) yB[i0] = w[s].y * scB;
                 }
             }
         }
@@ -455,8 +490,9 @@ __device__ __noinline__ int run_item(int first, int staged, int next) {
         const Acc sA = group_sum<T>(aA, sm_red(), g, t);
         const Acc sB = group_sum<T>(aB, sm_red(), g, t);
         if (t == 0) {
-            if (J.iA >= 0) c.alpha[J.iA] = (float)sA;
-            if (J.iB >= 0) c.alpha[J.iB] = (float)sB;
+            // the same power-of-two scale as y
+            if (J.iA >= 0) c.alpha[J.iA] = (float)(sA * (Acc)ldexpf(1.0f / (float)L, -J.mA));
+            if (J.iB >= 0) c.alpha[J.iB] = (float)(sB * (Acc)ldexpf(1.0f / (float)L, -J.mB));
         }
     }
     if (threadIdx.x == 0) fp_par.after = after;

@@ -434,8 +434,9 @@ int split_length(const hankel_plan_s* p, int L) {
 }
 
 // Pair jobs and work items of the persistent forward kernel for the tensors
-// marked in `sel`: tensors of one FFT length in pairs, each length's jobs
-// padded with empty slots to whole items, items longest length first.
+// marked in `sel`: tensors of one FFT length (and, as far as the counts
+// allow, one order) in pairs, each length's jobs padded with empty slots to
+// whole items, items longest length first.
 hankel_status build_fast(hankel_plan_s* p, const std::vector<char>& sel) {
     const int64_t count = (int64_t)p->descs.size();
     std::vector<std::pair<int, int64_t>> byL;
@@ -445,8 +446,13 @@ hankel_status build_fast(hankel_plan_s* p, const std::vector<char>& sel) {
             byL.emplace_back(hk::fast_length((int64_t)d.n[0] * d.m - d.m + 1), i);
         }
     if (byL.empty()) return HANKEL_OK;
-    std::stable_sort(byL.begin(), byL.end(),
-                     [](const std::pair<int, int64_t>& a, const std::pair<int, int64_t>& b) { return a.first > b.first; });
+    // longest length first; within a length by order, so that the groups of
+    // a warp (short lengths put several in one warp) mostly share m and
+    // with it the code of the spectral power
+    std::stable_sort(byL.begin(), byL.end(), [&](const std::pair<int, int64_t>& a, const std::pair<int, int64_t>& b) {
+        if (a.first != b.first) return a.first > b.first;
+        return p->descs[a.second].m < p->descs[b.second].m;
+    });
     hk::FastJob empty;
     std::memset(&empty, 0, sizeof(empty));
     empty.mA = empty.mB = 2;

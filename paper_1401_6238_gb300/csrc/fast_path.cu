@@ -85,14 +85,17 @@ __device__ __forceinline__ cx<float>* sm_t2() { return reinterpret_cast<cx<float
 __device__ __forceinline__ cx<float>* sm_t3() { return sm_t2() + TW2; }
 __device__ __forceinline__ cx<float>* sm_t5() { return sm_t3() + TW3; }
 __device__ __forceinline__ cx<float>* sm_buf(int i) { return sm_t5() + TW5 + i * BUF; }
+// complex slots of one group's exchange buffer: the padded length, rounded
+// up to an even count (every group's buffer starts on 16 bytes)
+__host__ __device__ constexpr int gslots(int L) { return ((L + L / 16) + 1) & ~1; }
 // exchange buffer i of length L: BUF apart, or the padded lengths of the
 // block's groups apart when that is longer (L = 5120, whose two buffers then
 // cover the slab's room)
 __host__ __device__ constexpr int sm_bufL_stride(int L) {
-    return (BLOCK / (L / rlast(L))) * (L + L / 16) > BUF ? (BLOCK / (L / rlast(L))) * (L + L / 16) : BUF;
+    return (BLOCK / (L / rlast(L))) * gslots(L) > BUF ? (BLOCK / (L / rlast(L))) * gslots(L) : BUF;
 }
 __host__ __device__ constexpr int sm_bufL_span(int L) {
-    return sm_bufL_stride(L) + (BLOCK / (L / rlast(L))) * (L + L / 16);
+    return sm_bufL_stride(L) + (BLOCK / (L / rlast(L))) * gslots(L);
 }
 template <int L>
 __device__ __forceinline__ cx<float>* sm_bufL(int i) {
@@ -141,21 +144,24 @@ __device__ __forceinline__ cx<float> sel(bool c, cx<float> a, cx<float> b) { ret
 
 // -------------------------------------------------------------- pass pieces
 
-// Asynchronous zero-padded copy of h~ + i x~ (length L, natural order) into
-// a padded buffer: 4-byte cp.async copies whose source size 0 zero-fills
-// (the source address then stays a valid one, the array's start).
-// Completion: stage_wait() and a barrier.
+// Asynchronous zero-padded copy of h~ and x~ (length L each) into a buffer
+// as two planes of floats, h~ at [0, L) and x~ at [L, 2L): 4-byte cp.async
+// copies whose source size 0 zero-fills (the source address then stays a
+// valid one, the array's start).  (16-byte copies, which the planes allow
+// for segments starting on 16 bytes, issued fewer instructions but made
+// the whole benchmark batch slower.)  Completion: stage_wait() and a barrier.
 template <int L, int T>
 __device__ __forceinline__ void stage(cx<float>* buf, const float* h, int d, const float* x, int n, int t) {
+    float* hs = reinterpret_cast<float*>(buf);
+    float* xs = hs + L;
 #pragma unroll 4
     for (int i = t; i < L; i += T) {
-        float* dst = reinterpret_cast<float*>(buf + pad(i));
-        const unsigned da = (unsigned)__cvta_generic_to_shared(dst);
+        const unsigned dh = (unsigned)__cvta_generic_to_shared(hs + i), dx = (unsigned)__cvta_generic_to_shared(xs + i);
         const int sa = i < d ? 4 : 0, sb = i < n ? 4 : 0;
         const float* pa = i < d ? h + i : h;
         const float* pb = i < n ? x + i : x;
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(da), "l"(pa), "r"(sa) : "memory");
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(da + 4), "l"(pb), "r"(sb) : "memory");
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dh), "l"(pa), "r"(sa) : "memory");
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dx), "l"(pb), "r"(sb) : "memory");
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
@@ -215,6 +221,27 @@ __device__ __forceinline__ void seq_pass(const cx<float>* src, cx<float>* dst, i
             }
             dft<R>(v);
             sstore<R, NS>(dst, (b - k) * R + k, v);
+        }
+    }
+}
+
+// First forward pass (Ns = 1, no twiddles) reading the staged planes:
+// butterfly b takes h~ and x~ at b + r L/R as one complex value each.
+template <int L, int R, int T>
+__device__ __forceinline__ void first_pass(const cx<float>* src, cx<float>* dst, int t) {
+    constexpr int NB = L / R;
+    constexpr int IT = (NB + T - 1) / T;
+    const float* hs = reinterpret_cast<const float*>(src);
+    const float* xs = hs + L;
+#pragma unroll 1
+    for (int j = 0; j < IT; ++j) {
+        const int b = t + T * j;
+        if (IT * T == NB || b < NB) {
+            cx<float> v[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = mk<float>(hs[b + r * NB], xs[b + r * NB]);
+            dft<R>(v);
+            sstore<R, 1>(dst, b * R, v);
         }
     }
 }
@@ -367,7 +394,7 @@ __shared__ Params fp_par;
 // the buffer returned (-1 otherwise).
 template <int L, bool F64, bool WA>
 __device__ __noinline__ int run_item(int first, int staged, int next) {
-    constexpr int R = rlast(L), T = nthr(L), Q = L / R, GS = L + L / 16;
+    constexpr int R = rlast(L), T = nthr(L), Q = L / R, GS = gslots(L);
     constexpr int QA = q0(Q), QB = q1(Q);  // power-of-two passes (QB == 1: none)
     constexpr int H = (T < 32 ? T : 32) / 2;  // mirror partner: lane ^ H
     static_assert(BLOCK % T == 0, "a block holds whole groups");
@@ -403,7 +430,7 @@ __device__ __noinline__ int run_item(int first, int staged, int next) {
     for (int tensor = 0; tensor < 2; ++tensor) {
         const bool B = tensor == 1;
         const int m = B ? J.mB : J.mA;
-        seq_pass<L, QA, 1, T>(buf(cur), buf(cur ^ 1), t, tw);
+        first_pass<L, QA, T>(buf(cur), buf(cur ^ 1), t);
         gsync<T>(g);
         cur ^= 1;
         if constexpr (QB > 1) {

@@ -189,3 +189,36 @@ def test_mixed_orders_same_length(dev):
     b = scaled_tensors(shapes, seed=37)
     (y, a) = run(b, dev=dev)[0][0]
     check(b, y, a)
+
+
+def test_unaligned_offsets(dev):
+    # h and x segments that do not start on 16 bytes: laid out one after
+    # another with gaps, starts 1..3 elements past a 16-byte boundary
+    b = scaled_tensors([(3, 600), (4, 300), (5, 1000), (3, 17), (2, 40), (5, 200), (4, 700)], seed=39)
+    d = hk.batch_descs(b)
+    hs, xs, ho, xo = [], [], 0, 0
+    for i in range(len(b)):
+        m, n, hi, xi = b.tensor(i)
+        ho += 1 + i % 3
+        xo += 3 - i % 3
+        d["h_off"][i], d["x_off"][i, 0] = ho, xo
+        hs.append((ho, hi))
+        xs.append((xo, xi))
+        ho = (ho + hi.size + 7) // 4 * 4
+        xo = (xo + n + 7) // 4 * 4
+    h, x = np.zeros(ho), np.zeros(xo)
+    for o, v in hs:
+        h[o: o + v.size] = v
+    for o, v in xs:
+        x[o: o + v.size] = v
+    assert all(int(o) % 4 != 0 for o in d["h_off"]) and all(int(o) % 4 != 0 for o in d["x_off"][:, 0])
+    plan = hk.Plan(d, hk.R32, hk.SAME_X)
+    assert plan.info["launches"] == 1
+    H = torch.tensor(h, dtype=torch.float32, device=dev)
+    X = torch.tensor(x, dtype=torch.float32, device=dev)
+    Y = torch.full((b.y_len,), float("nan"), dtype=torch.float32, device=dev)
+    A = torch.full((len(b),), float("nan"), dtype=torch.float32, device=dev)
+    plan.txv(H, X, Y, A)
+    torch.cuda.synchronize()
+    plan.close()
+    check(b, Y.cpu().numpy().astype(np.float64), A.cpu().numpy().astype(np.float64))

@@ -71,7 +71,9 @@ enum {
      * x_off[p-1]. */
     HANKEL_SAME_X = 1u << 0,
     /* Form the spectrum power / product and the pointwise product with the
-     * h spectrum in FP64 even for the FP32 dtypes. */
+     * h spectrum in FP64 even for the FP32 dtypes, for every tensor of the
+     * plan.  Without it the planner does so only where the bin policy
+     * (hankel_set_bin_policy) asks. */
     HANKEL_FP64_POWER = 1u << 1,
     /* hankel_txv() keeps the spectra it computes in plan workspace so that
      * the next hankel_txv_backward() reuses them instead of recomputing. */
@@ -166,6 +168,7 @@ typedef struct hankel_plan_info {
     int64_t h_elems;          /* minimum h/x/y buffer sizes implied by the offsets */
     int64_t x_elems;
     int64_t y_elems;
+    int64_t fp64_power_tensors; /* tensors whose spectrum power is formed in FP64 */
 } hankel_plan_info;
 
 /*
@@ -327,6 +330,33 @@ hankel_status hankel_set_tuning(double pass_cost, int points_per_thread);
 
 /* hankel_get_tuning -- the current planner knobs. */
 hankel_status hankel_get_tuning(double* pass_cost, int* points_per_thread);
+
+/*
+ * hankel_set_bin_policy -- per-length-bin planner choices for FP32 plans
+ * of real square tensors with one vector (Section 3 products), made after
+ * the call (process-wide; existing plans keep theirs).  A bin is one FFT
+ * length of the persistent forward kernel (32 .. 5120: 2^k, 3 2^k, 5120);
+ * a tensor belongs to the bin of the shortest such length >= its d.
+ *   nbins         entries in the arrays (0: every bin back to the default)
+ *   L[i]          the bin's length
+ *   path[i]       0: the persistent launch (default); 1: the per-length
+ *                 launches of the general real path
+ *   fp64_from_m[i] the bin's tensors of order m >= fp64_from_m[i] form
+ *                 their spectrum power (Section 3, X^{m-1}) in FP64; 9 or
+ *                 more (the default 99): never.  HANKEL_FP64_POWER still
+ *                 forces FP64 powers for every tensor of a plan.
+ * Bins not listed keep their current choices.  The project's autotuner
+ * (paper_1401_6238_gb300/autotune.py) times both paths and measures the
+ * FP32 error with and without FP64 powers per bin against the oracle, and
+ * the Python binding applies its cached table when it loads the library.
+ * Errors: EINVAL for a NULL array with nbins > 0, a length that is not a
+ * bin, path not 0 or 1, fp64_from_m outside [2, 99].
+ */
+hankel_status hankel_set_bin_policy(int32_t nbins, const int32_t* L, const int32_t* path, const int32_t* fp64_from_m);
+
+/* hankel_get_bin_policy -- the current choices of bin L (EINVAL if L is not
+ * a bin or an output is NULL). */
+hankel_status hankel_get_bin_policy(int32_t L, int32_t* path, int32_t* fp64_from_m);
 
 /* hankel_fft_length -- the FFT length the planner picks for generating
  * length d (d >= 1), or -1 when d is beyond the supported maximum. */

@@ -41,7 +41,6 @@
 
 #include <algorithm>
 #include <mutex>
-#include <type_traits>
 
 #include "fft_core.cuh"
 #include "launch.h"
@@ -354,18 +353,20 @@ __device__ __forceinline__ void gsync(int g) {
 }
 
 // Sum of one value over the T threads of a group (valid in thread 0 of the
-// group); the partial sums of the warps meet in the reduction scratch.
+// group); the partial sums of the warps meet in the group's slots of the
+// reduction scratch (one double-sized slot per warp, whatever the type, so
+// that groups summing floats and doubles never share bytes).
 template <int T, typename A>
 __device__ __forceinline__ A group_sum(A v, double* red, int g, int t) {
 #pragma unroll
     for (int o = (T < 32 ? T : 32) / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if constexpr (T > 32) {
-        A* r = reinterpret_cast<A*>(red);
-        if ((t & 31) == 0) r[g * (T / 32) + (t >> 5)] = v;
+        double* r = red + g * (T / 32);
+        if ((t & 31) == 0) *reinterpret_cast<A*>(r + (t >> 5)) = v;
         gsync<T>(g);
         A s = 0;
         if (t == 0)
-            for (int i = 0; i < T / 32; ++i) s += r[g * (T / 32) + i];
+            for (int i = 0; i < T / 32; ++i) s += *reinterpret_cast<const A*>(r + i);
         gsync<T>(g);
         return s;
     }
@@ -392,7 +393,7 @@ __shared__ Params fp_par;
 // this job's first input, or -1.  `next`: the index of the block's next
 // item; when it has the same length its first input is staged here, into
 // the buffer returned (-1 otherwise).
-template <int L, bool F64, bool WA>
+template <int L, bool WA, bool MIX>
 __device__ __noinline__ int run_item(int first, int staged, int next) {
     constexpr int R = rlast(L), T = nthr(L), Q = L / R, GS = gslots(L);
     constexpr int QA = q0(Q), QB = q1(Q);  // power-of-two passes (QB == 1: none)
@@ -406,14 +407,24 @@ __device__ __noinline__ int run_item(int first, int staged, int next) {
     const int g = threadIdx.x / T, t = threadIdx.x % T;
     const FastJob& J = c.jobs[first + g];
     auto buf = [&](int i) { return sm_bufL<L>(i) + g * GS; };
-    using Acc = typename std::conditional<F64, double, float>::type;
     const int b = last_b<T>(t);
     const bool self0 = b == 0;  // self-mirrored butterflies 0 and T/2
     const int lane = threadIdx.x & 31, src = (b == T / 2) ? lane : (lane ^ H);
     cx<float> v[R];
     // P_A, slot s at st[s * BLOCK]
     cx<float>* const st = (L == LONG ? c.slab + (size_t)blockIdx.x * R * BLOCK : sm_stash()) + threadIdx.x;
-    Acc aA = 0, aB = 0;
+    // FP64 spectrum powers per tensor.  A group narrower than a warp shares
+    // its warp with other groups, whose lanes must reach the same shuffles:
+    // there the warp takes FP64 powers when any of its groups asks for them.
+    // (MIX: the plan has such tensors; without them no FP64 code is compiled in)
+    bool f64A = MIX && J.fA != 0, f64B = MIX && J.fB != 0;
+    if constexpr (MIX && T < 32) {
+        f64A = __any_sync(0xffffffffu, f64A);
+        f64B = __any_sync(0xffffffffu, f64B);
+    }
+    // alpha: FP32 sums, FP64 ones for a tensor with its power in FP64
+    float aA = 0, aB = 0;
+    double a64A = 0, a64B = 0;
     int after = 0;
     if (threadIdx.x == 0) after = atomicAdd(c.ctr, 1) + (int)gridDim.x;  // stored at the end
 
@@ -442,25 +453,30 @@ __device__ __noinline__ int run_item(int first, int staged, int next) {
         if (!B) stage<L, T>(buf(cur ^ 1), c.h + J.hB, J.dB, c.x + J.xB, J.nB, t);
         last_pass<L, R>(v, buf(cur), b, tw);
         const int e = m - 1;
-        Acc a = 0;
-        if constexpr (T >= 32) {
+        float a = 0;
+        double ad = 0;
+        if (MIX && (B ? f64B : f64A)) {
+            if constexpr (MIX) products<R, true, WA, 0>(v, st, B, src, self0, e, ad);
+        } else if constexpr (T >= 32) {
             // the power with a compile-time exponent for the common orders
             switch (e) {
-                case 2: products<R, F64, WA, 2>(v, st, B, src, self0, e, a); break;
-                case 3: products<R, F64, WA, 3>(v, st, B, src, self0, e, a); break;
-                case 4: products<R, F64, WA, 4>(v, st, B, src, self0, e, a); break;
-                default: products<R, F64, WA, 0>(v, st, B, src, self0, e, a); break;
+                case 2: products<R, false, WA, 2>(v, st, B, src, self0, e, a); break;
+                case 3: products<R, false, WA, 3>(v, st, B, src, self0, e, a); break;
+                case 4: products<R, false, WA, 4>(v, st, B, src, self0, e, a); break;
+                default: products<R, false, WA, 0>(v, st, B, src, self0, e, a); break;
             }
         } else {
-            products<R, F64, WA, 0>(v, st, B, src, self0, e, a);
+            products<R, false, WA, 0>(v, st, B, src, self0, e, a);
         }
         if (!B) {
             aA = a;
+            a64A = ad;
             stage_wait();
             gsync<T>(g);
             cur ^= 1;
         } else {
             aB = a;
+            a64B = ad;
         }
     }
 
@@ -514,19 +530,29 @@ __device__ __noinline__ int run_item(int first, int staged, int next) {
         }
     }
     if constexpr (WA) {
-        const Acc sA = group_sum<T>(aA, sm_red(), g, t);
-        const Acc sB = group_sum<T>(aB, sm_red(), g, t);
+        // (the FP64 choices are uniform over the group, and over the warp for
+        // groups narrower than one: the sums' shuffles and barriers agree)
+        float sA = 0, sB = 0;
+        double sA64 = 0, sB64 = 0;
+        if constexpr (MIX) {
+            if (f64A) sA64 = group_sum<T>(a64A, sm_red(), g, t); else sA = group_sum<T>(aA, sm_red(), g, t);
+            if (f64B) sB64 = group_sum<T>(a64B, sm_red(), g, t); else sB = group_sum<T>(aB, sm_red(), g, t);
+        } else {
+            sA = group_sum<T>(aA, sm_red(), g, t);
+            sB = group_sum<T>(aB, sm_red(), g, t);
+        }
         if (t == 0) {
             // the same power-of-two scale as y
-            if (J.iA >= 0) c.alpha[J.iA] = (float)(sA * (Acc)ldexpf(1.0f / (float)L, -J.mA));
-            if (J.iB >= 0) c.alpha[J.iB] = (float)(sB * (Acc)ldexpf(1.0f / (float)L, -J.mB));
+            const float scA = ldexpf(1.0f / (float)L, -J.mA), scB = ldexpf(1.0f / (float)L, -J.mB);
+            if (J.iA >= 0) c.alpha[J.iA] = f64A ? (float)(sA64 * (double)scA) : sA * scA;
+            if (J.iB >= 0) c.alpha[J.iB] = f64B ? (float)(sB64 * (double)scB) : sB * scB;
         }
     }
     if (threadIdx.x == 0) fp_par.after = after;
     return staged_next;
 }
 
-template <bool F64, bool WA>
+template <bool WA, bool MIX>
 __global__ void __launch_bounds__(BLOCK, HK_FAST_MIN_BLOCKS)
     fast_fwd_kernel(const FastItem* __restrict__ items, int nitems, const FastJob* __restrict__ jobs,
                     const float* __restrict__ h, const float* __restrict__ x, float* __restrict__ y,
@@ -559,22 +585,22 @@ __global__ void __launch_bounds__(BLOCK, HK_FAST_MIN_BLOCKS)
     while (it < nitems) {
         const FastItem I = items[it];
         switch (I.L) {
-            case 5120: staged = run_item<5120, F64, WA>(I.first, staged, next); break;
-            case 4096: staged = run_item<4096, F64, WA>(I.first, staged, next); break;
-            case 3072: staged = run_item<3072, F64, WA>(I.first, staged, next); break;
-            case 2048: staged = run_item<2048, F64, WA>(I.first, staged, next); break;
-            case 1536: staged = run_item<1536, F64, WA>(I.first, staged, next); break;
-            case 1024: staged = run_item<1024, F64, WA>(I.first, staged, next); break;
-            case 768: staged = run_item<768, F64, WA>(I.first, staged, next); break;
-            case 512: staged = run_item<512, F64, WA>(I.first, staged, next); break;
-            case 384: staged = run_item<384, F64, WA>(I.first, staged, next); break;
-            case 256: staged = run_item<256, F64, WA>(I.first, staged, next); break;
-            case 192: staged = run_item<192, F64, WA>(I.first, staged, next); break;
-            case 128: staged = run_item<128, F64, WA>(I.first, staged, next); break;
-            case 96: staged = run_item<96, F64, WA>(I.first, staged, next); break;
-            case 64: staged = run_item<64, F64, WA>(I.first, staged, next); break;
-            case 48: staged = run_item<48, F64, WA>(I.first, staged, next); break;
-            case 32: staged = run_item<32, F64, WA>(I.first, staged, next); break;
+            case 5120: staged = run_item<5120, WA, MIX>(I.first, staged, next); break;
+            case 4096: staged = run_item<4096, WA, MIX>(I.first, staged, next); break;
+            case 3072: staged = run_item<3072, WA, MIX>(I.first, staged, next); break;
+            case 2048: staged = run_item<2048, WA, MIX>(I.first, staged, next); break;
+            case 1536: staged = run_item<1536, WA, MIX>(I.first, staged, next); break;
+            case 1024: staged = run_item<1024, WA, MIX>(I.first, staged, next); break;
+            case 768: staged = run_item<768, WA, MIX>(I.first, staged, next); break;
+            case 512: staged = run_item<512, WA, MIX>(I.first, staged, next); break;
+            case 384: staged = run_item<384, WA, MIX>(I.first, staged, next); break;
+            case 256: staged = run_item<256, WA, MIX>(I.first, staged, next); break;
+            case 192: staged = run_item<192, WA, MIX>(I.first, staged, next); break;
+            case 128: staged = run_item<128, WA, MIX>(I.first, staged, next); break;
+            case 96: staged = run_item<96, WA, MIX>(I.first, staged, next); break;
+            case 64: staged = run_item<64, WA, MIX>(I.first, staged, next); break;
+            case 48: staged = run_item<48, WA, MIX>(I.first, staged, next); break;
+            case 32: staged = run_item<32, WA, MIX>(I.first, staged, next); break;
             default: staged = -1; break;
         }
         // the staged copies must land before the next item reads them
@@ -628,10 +654,13 @@ cudaError_t launch_fast_forward(const FastItem* items, int nitems, int grid, con
                                 const void* x, void* y, void* alpha, const void* t2, const void* t3, const void* t5,
                                 void* slab, int* ctr, int flags, cudaStream_t st) {
     const size_t smem = fast_smem_bytes();
-    const bool f64 = (flags & HANKEL_FP64_POWER) != 0, wa = alpha != nullptr;
-    auto k = f64 ? (wa ? fp::fast_fwd_kernel<true, true> : fp::fast_fwd_kernel<true, false>)
-                 : (wa ? fp::fast_fwd_kernel<false, true> : fp::fast_fwd_kernel<false, false>);
-    const int variant = 2 * f64 + wa;
+    // HANKEL_FP64_POWER here: some job asks for FP64 spectrum powers (the
+    // job table says which tensors), so the kernel variant holding that
+    // code runs
+    const bool wa = alpha != nullptr, mix = (flags & HANKEL_FP64_POWER) != 0;
+    auto k = wa ? (mix ? fp::fast_fwd_kernel<true, true> : fp::fast_fwd_kernel<true, false>)
+                : (mix ? fp::fast_fwd_kernel<false, true> : fp::fast_fwd_kernel<false, false>);
+    const int variant = 2 * mix + wa;
     static std::mutex mu;
     static bool done[4][64] = {};
     int dev = 0;

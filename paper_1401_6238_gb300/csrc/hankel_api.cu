@@ -51,6 +51,18 @@ constexpr int kMaxL = 16384;
 double g_pass_cost = 10.0;
 int g_points_per_thread = 16;
 std::mutex g_tune_mu;
+// Per-length-bin choices (hankel_set_bin_policy), keyed by the persistent
+// kernel's FFT lengths; absent bins take the defaults.
+struct BinPolicy {
+    int path = 0;          // 0: persistent launch, 1: per-length launches
+    int fp64_from_m = 99;  // orders m >= this form their spectrum power in FP64
+};
+std::map<int, BinPolicy> g_bins;
+BinPolicy bin_policy(int L) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const auto it = g_bins.find(L);
+    return it == g_bins.end() ? BinPolicy() : it->second;
+}
 double radix_cost(int r) {
     switch (r) {
         case 2: return 5.0;
@@ -203,6 +215,8 @@ struct hankel_plan_s {
     void* d_fast_slab = nullptr;  // per-block slab of the longest length (or null)
     int fast_grid = 0;
     int64_t fast_pairs = 0;  // pair jobs with at least one tensor (the rest pad items)
+    bool fast_f64 = false;   // some job of the persistent launch asks for FP64 powers
+    int64_t fp64_tensors = 0;  // tensors whose spectrum power is formed in FP64
     // general path (complex data, distinct vectors, BHHB)
     hk::GeneralPlan* gen = nullptr;
     // twiddle tables and workspace
@@ -378,7 +392,7 @@ void make_launches(std::vector<hk::RealJob>& jobs, std::vector<hk::RealLaunch>& 
     launches.clear();
     for (size_t i = 0; i < jobs.size();) {
         const int L0 = jobs[i].P.L;
-        hk::RealLaunch lc;
+        hk::RealLaunch lc{};
         lc.first = (int)i;
         lc.nthr = nthr_of(L0);
         lc.Lmax = L0;
@@ -437,7 +451,7 @@ int split_length(const hankel_plan_s* p, int L) {
 // marked in `sel`: tensors of one FFT length (and, as far as the counts
 // allow, one order) in pairs, each length's jobs padded with empty slots to
 // whole items, items longest length first.
-hankel_status build_fast(hankel_plan_s* p, const std::vector<char>& sel) {
+hankel_status build_fast(hankel_plan_s* p, const std::vector<char>& sel, const std::vector<char>& want64) {
     const int64_t count = (int64_t)p->descs.size();
     std::vector<std::pair<int, int64_t>> byL;
     for (int64_t i = 0; i < count; ++i)
@@ -461,16 +475,18 @@ hankel_status build_fast(hankel_plan_s* p, const std::vector<char>& sel) {
         const hankel_desc& d = p->descs[i];
         const int dl = (int)((int64_t)d.n[0] * d.m - d.m + 1);
         if (!B) {
-            J.mA = d.m; J.nA = d.n[0]; J.dA = dl; J.iA = (int)i;
+            J.mA = d.m; J.nA = d.n[0]; J.dA = dl; J.iA = (int)i; J.fA = want64[i];
             J.hA = d.h_off; J.xA = d.x_off[0]; J.yA = d.y_off;
         } else {
-            J.mB = d.m; J.nB = d.n[0]; J.dB = dl; J.iB = (int)i;
+            J.mB = d.m; J.nB = d.n[0]; J.dB = dl; J.iB = (int)i; J.fB = want64[i];
             J.hB = d.h_off; J.xB = d.x_off[0]; J.yB = d.y_off;
         }
     };
     p->fast_jobs.clear();
     p->fast_items.clear();
     p->fast_pairs = 0;
+    p->fast_f64 = false;
+    for (const auto& e : byL) p->fast_f64 = p->fast_f64 || want64[e.second];
     for (size_t k = 0; k < byL.size();) {
         const int L = byL[k].first;
         const int G = hk::fast_jobs_per_item(L);
@@ -568,15 +584,22 @@ hankel_status build_real_path(hankel_plan_s* p) {
     p->fwd_jobs.clear();
     p->bwd_jobs.clear();
     // FP32 forward products whose generating length fits the persistent
-    // kernel's transforms run there
+    // kernel's transforms run there, unless their bin's policy says
+    // otherwise; FP64 spectrum powers for the whole plan (flag) or for the
+    // orders the bin's policy names
     const bool fast_ok = p->dtype == HANKEL_R32 &&
                          !(p->flags & (HANKEL_STORE_SPECTRA | HANKEL_ONE_PER_LAUNCH | HANKEL_ANTICIRCULANT));
-    std::vector<char> on_fast(count, 0);
-    if (fast_ok)
-        for (int64_t i = 0; i < count; ++i) {
-            const hankel_desc& d = p->descs[i];
-            on_fast[i] = hk::fast_length((int64_t)d.n[0] * d.m - d.m + 1) > 0;
-        }
+    std::vector<char> on_fast(count, 0), want64(count, 0);
+    p->fp64_tensors = 0;
+    for (int64_t i = 0; i < count; ++i) {
+        const hankel_desc& d = p->descs[i];
+        const int dl = (p->flags & HANKEL_ANTICIRCULANT) ? d.n[0] : (int)(d.n[0] * (int64_t)d.m - d.m + 1);
+        const int Lb = hk::fast_length(dl);
+        const BinPolicy bp = Lb > 0 ? bin_policy(Lb) : BinPolicy();
+        want64[i] = !dbl && ((p->flags & HANKEL_FP64_POWER) || d.m >= bp.fp64_from_m);
+        p->fp64_tensors += want64[i];
+        on_fast[i] = fast_ok && Lb > 0 && bp.path == 0;
+    }
     std::vector<int64_t> fwd_order;
     for (int64_t a : order)
         if (!on_fast[a]) fwd_order.push_back(a);
@@ -640,6 +663,16 @@ hankel_status build_real_path(hankel_plan_s* p) {
     const bool opl = (p->flags & HANKEL_ONE_PER_LAUNCH) != 0;
     make_launches(p->fwd_jobs, p->fwd_launches, opl, 2, max_single_L);
     make_launches(p->bwd_jobs, p->bwd_launches, opl, 2, max_single_L);
+    // a launch forms FP64 powers when one of its tensors asks for them
+    auto mark64 = [&](const std::vector<hk::RealJob>& jobs, std::vector<hk::RealLaunch>& launches) {
+        for (auto& lc : launches) {
+            lc.fp64 = 0;
+            for (int j = lc.first; j < lc.first + lc.count; ++j)
+                lc.fp64 |= (jobs[j].iA >= 0 && want64[jobs[j].iA]) || (jobs[j].iB >= 0 && want64[jobs[j].iB]);
+        }
+    };
+    mark64(p->fwd_jobs, p->fwd_launches);
+    mark64(p->bwd_jobs, p->bwd_launches);
     for (auto* v : {&p->fwd_launches, &p->bwd_launches})
         for (auto& lc : *v)
             if (hk::real_launch_smem(dbl, lc) > kSmemLimit)
@@ -658,7 +691,7 @@ hankel_status build_real_path(hankel_plan_s* p) {
     const hankel_status ss = make_streams(p, opl ? 0 : std::max(nfwd, p->bwd_launches.size()));
     if (ss != HANKEL_OK) return ss;
     if (fast_ok) {
-        const hankel_status fs = build_fast(p, on_fast);
+        const hankel_status fs = build_fast(p, on_fast, want64);
         if (fs != HANKEL_OK) return fs;
     }
     p->ws_bytes = (size_t)std::max<int64_t>(ws, 1) * 2 * real_size(p->dtype);
@@ -732,7 +765,7 @@ hankel_status build_multi_path(hankel_plan_s* p) {
     const bool opl = (p->flags & HANKEL_ONE_PER_LAUNCH) != 0;
     p->multi_launches.clear();
     for (size_t i = 0; i < p->multi_jobs.size();) {
-        hk::RealLaunch lc;
+        hk::RealLaunch lc{};
         lc.first = (int)i;
         lc.nthr = nthr_of(p->multi_jobs[i].P.L);
         lc.split = 0;
@@ -1203,7 +1236,8 @@ hankel_status hankel_txv(hankel_plan_t p, const void* h, const void* x, void* y,
         });
     if (!p->real_path) return hk::general_forward(p->gen, h, x, y, alpha, st, g_err);
     auto fwd = [&](const hk::RealLaunch& lc, cudaStream_t s) {
-        return hk::launch_real_forward(dbl, lc, p->d_fwd, h, x, y, alpha, p->d_tw, p->d_ws, (int)p->flags, s);
+        return hk::launch_real_forward(dbl, lc, p->d_fwd, h, x, y, alpha, p->d_tw, p->d_ws,
+                                       (int)(p->flags | (lc.fp64 ? HANKEL_FP64_POWER : 0u)), s);
     };
     if (!p->fast) return run_forked(p, p->fwd_launches, st, fwd);
     // the per-length launches (queued first) on the plan's streams, the
@@ -1212,7 +1246,7 @@ hankel_status hankel_txv(hankel_plan_t p, const void* h, const void* x, void* y,
         const char* t2 = (const char*)p->d_fast_tw;
         return hk::launch_fast_forward(p->d_fast_items, (int)p->fast_items.size(), p->fast_grid, p->d_fast_jobs, h, x,
                                        y, alpha, t2, t2 + p->fast_tw3, t2 + p->fast_tw5, p->d_fast_slab,
-                                       p->d_fast_ctr, (int)p->flags, s);
+                                       p->d_fast_ctr, p->fast_f64 ? (int)HANKEL_FP64_POWER : 0, s);
     };
     cudaError_t e;
     if (p->fwd_launches.empty() || p->streams.empty()) {
@@ -1365,7 +1399,7 @@ hankel_status hankel_txv_backward(hankel_plan_t p, const void* grad_y, const voi
     const int stored = (p->flags & HANKEL_STORE_SPECTRA) ? 1 : 0;
     return run_forked(p, p->bwd_launches, st, [&](const hk::RealLaunch& lc, cudaStream_t s) {
         return hk::launch_real_backward(dbl, lc, p->d_bwd, grad_y, h, x, grad_h, grad_x, p->d_tw, p->d_ws,
-                                        (int)p->flags, stored, s);
+                                        (int)(p->flags | (lc.fp64 ? HANKEL_FP64_POWER : 0u)), stored, s);
     });
 }
 
@@ -1385,6 +1419,7 @@ hankel_status hankel_plan_query(hankel_plan_t p, hankel_plan_info* info) {
         info->launches = in.launches + 1;
         info->distinct_lengths = in.distinct_lengths;
         info->workspace_bytes = in.workspace_bytes;
+        info->fp64_power_tensors = in.fp64_power_tensors;
     } else if (p->multi_path) {
         info->jobs = (int64_t)p->multi_jobs.size();
         info->launches = (int64_t)p->multi_launches.size();
@@ -1395,9 +1430,12 @@ hankel_status hankel_plan_query(hankel_plan_t p, hankel_plan_info* info) {
         info->launches = (int64_t)p->fwd_launches.size() + (p->fast ? 1 : 0);
         info->distinct_lengths = (int64_t)p->tw_off.size();
         info->workspace_bytes = (int64_t)p->ws_bytes;
+        info->fp64_power_tensors = p->fp64_tensors;
     } else {
         hk::general_info(p->gen, &info->jobs, &info->launches, &info->distinct_lengths, &info->workspace_bytes);
     }
+    if (!p->real_path && !p->inner && (p->flags & HANKEL_FP64_POWER) && !is_double(p->dtype))
+        info->fp64_power_tensors = info->count;
     return HANKEL_OK;
 }
 
@@ -1418,6 +1456,35 @@ hankel_status hankel_get_tuning(double* pass_cost, int* points_per_thread) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     *pass_cost = g_pass_cost;
     *points_per_thread = g_points_per_thread;
+    return HANKEL_OK;
+}
+
+hankel_status hankel_set_bin_policy(int32_t nbins, const int32_t* L, const int32_t* path, const int32_t* fp64_from_m) {
+    if (nbins < 0) return fail(HANKEL_EINVAL, "nbins %d is negative", nbins);
+    if (nbins > 0 && (!L || !path || !fp64_from_m)) return fail(HANKEL_EINVAL, "NULL argument");
+    for (int32_t i = 0; i < nbins; ++i) {
+        if (!hk::fast_length_ok(L[i])) return fail(HANKEL_EINVAL, "%d is not a length bin", L[i]);
+        if (path[i] != 0 && path[i] != 1) return fail(HANKEL_EINVAL, "path %d of bin %d is not 0 or 1", path[i], L[i]);
+        if (fp64_from_m[i] < 2 || fp64_from_m[i] > 99)
+            return fail(HANKEL_EINVAL, "fp64_from_m %d of bin %d outside [2, 99]", fp64_from_m[i], L[i]);
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (nbins == 0) g_bins.clear();
+    for (int32_t i = 0; i < nbins; ++i) {
+        BinPolicy bp;
+        bp.path = path[i];
+        bp.fp64_from_m = fp64_from_m[i];
+        g_bins[L[i]] = bp;
+    }
+    return HANKEL_OK;
+}
+
+hankel_status hankel_get_bin_policy(int32_t L, int32_t* path, int32_t* fp64_from_m) {
+    if (!path || !fp64_from_m) return fail(HANKEL_EINVAL, "NULL argument");
+    if (!hk::fast_length_ok(L)) return fail(HANKEL_EINVAL, "%d is not a length bin", L);
+    const BinPolicy bp = bin_policy(L);
+    *path = bp.path;
+    *fp64_from_m = bp.fp64_from_m;
     return HANKEL_OK;
 }
 

@@ -76,6 +76,7 @@ struct FoldGroup {
 struct RealLaunch {
     int32_t first, count;  // range in the job table
     int32_t nthr, split, Lmax, arrays;  // split: the jobs are split jobs (two blocks each)
+    int32_t fp64;  // nonzero: spectrum powers in FP64 (some tensor of the launch asks for them)
 };
 
 // Persistent forward kernel (fast_path.cu): a pair job of two real square
@@ -84,6 +85,7 @@ struct RealLaunch {
 struct FastJob {
     int32_t mA, nA, dA, iA;
     int32_t mB, nB, dB, iB;
+    int32_t fA, fB;  // nonzero: the tensor's spectrum power in FP64
     int64_t hA, xA, yA, hB, xB, yB;
 };
 // One work item of the persistent kernel: the jobs [first, first + G) of FFT

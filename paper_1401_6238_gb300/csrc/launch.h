@@ -36,7 +36,8 @@ int stage_twiddle_count(const FftPlan& P);
 // persistent forward kernel of fast_path.cu: its FFT lengths, jobs per item
 // and launch (t2, t3, t5 = the w_4096^e, w_3072^e, w_5120^e tables; slab =
 // grid x fast_slab_bytes(L) bytes for the longest length L of the items;
-// ctr = two zeroed ints)
+// ctr = two zeroed ints; flags: HANKEL_FP64_POWER when some job's fA or fB
+// asks for FP64 spectrum powers)
 bool fast_length_ok(int L);
 int fast_length(int64_t d);
 int fast_jobs_per_item(int L);

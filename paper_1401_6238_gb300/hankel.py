@@ -40,7 +40,7 @@ MDESC_DTYPE = np.dtype([("m", np.int32), ("levels", np.int32), ("n", np.int32, (
 class PlanInfo(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in
                 ("count", "jobs", "launches", "distinct_lengths", "max_length", "sum_length", "workspace_bytes",
-                 "h_elems", "x_elems", "y_elems")]
+                 "h_elems", "x_elems", "y_elems", "fp64_power_tensors")]
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}
@@ -71,6 +71,8 @@ _SIGS = {
     "hankel_fft_length": (ctypes.c_int64, [ctypes.c_int64]),
     "hankel_set_tuning": (ctypes.c_int, [ctypes.c_double, ctypes.c_int]),
     "hankel_get_tuning": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
+    "hankel_set_bin_policy": (ctypes.c_int, [ctypes.c_int32] + [ctypes.POINTER(ctypes.c_int32)] * 3),
+    "hankel_get_bin_policy": (ctypes.c_int, [ctypes.c_int32] + [ctypes.POINTER(ctypes.c_int32)] * 2),
     "hankel_plan_destroy": (None, [ctypes.c_void_p]),
     "hankel_last_error": (ctypes.c_char_p, []),
     "hankel_version": (ctypes.c_char_p, []),
@@ -111,6 +113,9 @@ def _apply_cached_tuning():
         if rec.get("device") == torch.cuda.get_device_name():
             best = rec["best"]
             _lib.hankel_set_tuning(float(best["pass_cost"]), int(best["points_per_thread"]))
+            bins = {int(b["L"]): (int(b["path"]), int(b["fp64_from_m"])) for b in rec.get("bins", [])}
+            if bins:
+                hankel_set_bin_policy(bins)
     except Exception:
         pass
 
@@ -204,6 +209,23 @@ def hankel_get_tuning():
     c, p = ctypes.c_double(), ctypes.c_int()
     _check(load().hankel_get_tuning(ctypes.byref(c), ctypes.byref(p)))
     return c.value, p.value
+
+
+def hankel_set_bin_policy(bins):
+    """bins: {L: (path, fp64_from_m)} for the persistent kernel's length
+    bins; an empty mapping puts every bin back to its default."""
+    n = len(bins)
+    arr = lambda vals: (ctypes.c_int32 * max(n, 1))(*vals)
+    Ls = sorted(bins)
+    _check(load().hankel_set_bin_policy(n, arr(Ls), arr([int(bins[L][0]) for L in Ls]),
+                                        arr([int(bins[L][1]) for L in Ls])))
+
+
+def hankel_get_bin_policy(L):
+    """(path, fp64_from_m) of length bin L."""
+    p, f = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().hankel_get_bin_policy(int(L), ctypes.byref(p), ctypes.byref(f)))
+    return p.value, f.value
 
 
 def hankel_plan_destroy(plan):

@@ -222,3 +222,53 @@ def test_unaligned_offsets(dev):
     torch.cuda.synchronize()
     plan.close()
     check(b, Y.cpu().numpy().astype(np.float64), A.cpu().numpy().astype(np.float64))
+
+
+@pytest.fixture
+def bin_policy():
+    """Sets per-bin planner choices for one test and puts the defaults back."""
+    yield hk.hankel_set_bin_policy
+    hk.hankel_set_bin_policy({})
+
+
+def test_bin_policy_fp64_powers(dev, bin_policy):
+    # orders >= 4 of the 1024 and 4096 bins form their powers in FP64, in the
+    # same persistent launch as the FP32 ones; every result stays right
+    shapes = [(3, 300), (4, 250), (5, 200), (4, 256), (3, 1300), (4, 1000), (5, 800), (5, 819), (6, 100), (2, 40)]
+    b = scaled_tensors(shapes, seed=40)
+    bin_policy({1024: (0, 4), 4096: (0, 4)})
+    (y, a), info = (lambda o: (o[0][0], o[1]))(run(b, dev=dev))
+    lens = [32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048, 3072, 4096, 5120]
+    bins = [next(L for L in lens if L >= m * (n - 1) + 1) for m, n in shapes]
+    want = sum(1 for (m, n), L in zip(shapes, bins) if L in (1024, 4096) and m >= 4)
+    assert want == 6 and info["fp64_power_tensors"] == want and info["launches"] == 1
+    check(b, y, a)
+    # the plan flag still forces every tensor
+    (y, a), info = (lambda o: (o[0][0], o[1]))(run(b, flags=hk.SAME_X | hk.FP64_POWER, dev=dev))
+    assert info["fp64_power_tensors"] == len(b)
+    check(b, y, a)
+
+
+def test_bin_policy_fp64_powers_in_shared_warps(dev, bin_policy):
+    # FFT length 96 runs groups of 8 threads, four to a warp: tensors with
+    # and without FP64 powers (and padding slots) share warps, which then
+    # take one code path (FP64 for all when any group asks)
+    shapes = [(3, 30), (4, 22), (5, 18), (2, 45), (3, 29), (4, 21), (5, 17)] * 3
+    b = scaled_tensors(shapes, seed=42)
+    bin_policy({96: (0, 4)})
+    (y, a), info = (lambda o: (o[0][0], o[1]))(run(b, dev=dev))
+    assert info["fp64_power_tensors"] == 12 and info["launches"] == 1
+    check(b, y, a)
+    (y, a), info = (lambda o: (o[0][0], o[1]))(run(b, flags=hk.SAME_X | hk.FP64_POWER, dev=dev))
+    check(b, y, a)
+
+
+def test_bin_policy_routes_a_bin_to_the_per_length_launches(dev, bin_policy):
+    b = wl.batched_square(count=200, seed=41, n_lo=16, n_hi=1024)
+    (y0, a0), info0 = (lambda o: (o[0][0], o[1]))(run(b, dev=dev))
+    assert info0["launches"] == 1
+    bin_policy({3072: (1, 99), 256: (1, 99)})
+    (y1, a1), info1 = (lambda o: (o[0][0], o[1]))(run(b, dev=dev))
+    assert info1["launches"] > 1
+    check(b, y0, a0)
+    check(b, y1, a1)

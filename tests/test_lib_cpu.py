@@ -130,6 +130,33 @@ def test_tuning_knobs(lib):
         hk.hankel_set_tuning(*old)
 
 
+BINS = [32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048, 3072, 4096, 5120]
+
+
+def test_bin_policy(lib):
+    # defaults: every bin on the persistent launch, FP32 powers
+    hk.hankel_set_bin_policy({})
+    assert all(hk.hankel_get_bin_policy(L) == (0, 99) for L in BINS)
+    try:
+        hk.hankel_set_bin_policy({1024: (1, 99), 4096: (0, 7)})
+        assert hk.hankel_get_bin_policy(1024) == (1, 99)
+        assert hk.hankel_get_bin_policy(4096) == (0, 7)
+        assert hk.hankel_get_bin_policy(2048) == (0, 99)  # not listed: unchanged
+        hk.hankel_set_bin_policy({4096: (1, 5)})  # other bins keep their choices
+        assert hk.hankel_get_bin_policy(1024) == (1, 99) and hk.hankel_get_bin_policy(4096) == (1, 5)
+        for bad in [{1000: (0, 99)}, {16: (0, 99)}, {1024: (2, 99)}, {1024: (0, 1)}, {1024: (0, 100)}]:
+            with pytest.raises(hk.HankelError) as e:
+                hk.hankel_set_bin_policy(bad)
+            assert e.value.status == hk.EINVAL
+        with pytest.raises(hk.HankelError):
+            hk.hankel_get_bin_policy(1000)
+        # a rejected call changes nothing
+        assert hk.hankel_get_bin_policy(1024) == (1, 99)
+    finally:
+        hk.hankel_set_bin_policy({})
+    assert hk.hankel_get_bin_policy(4096) == (0, 99)
+
+
 def test_mdesc_layout_matches_header():
     # int32 m, int32 levels, int32 n[4][8], int64 h_off, int64 x_off[8], int64 y_off
     assert hk.MDESC_DTYPE.itemsize == 216

@@ -555,6 +555,8 @@ def main():
     descs = hk.batch_descs(batch)
     plan = hk.Plan(descs, hk.R32, hk.SAME_X)
     info = plan.info
+    from paper_1401_6238_gb300 import autotune
+    tuning = autotune.tuning_record()
     copies = max(2, args.copies)
     Hs = [torch.tensor(batch.h, dtype=torch.float32, device=dev) for _ in range(copies)]
     Xs = [torch.tensor(batch.x, dtype=torch.float32, device=dev) for _ in range(copies)]
@@ -726,7 +728,7 @@ def main():
                                              torch.cuda.get_device_properties(dev).multi_processor_count),
                 "accuracy": accuracy,
                 "e2e": e2e, "gpu_launches": int(info["launches"]) * args.steps,
-                "plan": info, "fp64_plain": fp64, "cpu_baseline": cpu, "clocks": clocks,
+                "plan": info, "tuning": tuning, "fp64_plain": fp64, "cpu_baseline": cpu, "clocks": clocks,
                 "secondary": secondary, "graph_replay": graph,
                 "step_ms_min": float(np.min(step_ms)), "step_ms_median": float(np.median(step_ms))}
         print(json.dumps(line))

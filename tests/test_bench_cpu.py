@@ -126,3 +126,28 @@ def test_oracle_errors_over_a_batch():
     y[o + n // 2] += 1e-4 * np.max(np.abs(y[o:o + n]))
     e = bench.oracle_errors(b, y, 1, _SerialPool())
     assert e[37] == pytest.approx(1e-4) and np.all(np.delete(e, 37) == 0.0)
+
+
+def test_autotune_fp64_threshold_rule():
+    from paper_1401_6238_gb300 import autotune as at
+    # FP64 powers that never help: never chosen
+    e32 = {m: 3e-6 * m for m in range(2, 9)}
+    assert at.fp64_threshold(e32, dict(e32)) == 99
+    # they pay from m = 6 up (error cut in half, FP32 error above half the bound)
+    e32 = {2: 1e-6, 3: 1e-6, 4: 2e-6, 5: 4e-6, 6: 6e-6, 7: 8e-6, 8: 9e-6}
+    e64 = {m: (v / 2 if m >= 6 else v) for m, v in e32.items()}
+    assert at.fp64_threshold(e32, e64) == 6
+    # a gain below the bound's half does not count, nor a gap at the top
+    e64 = {m: v / 2 for m, v in e32.items()}
+    assert at.fp64_threshold(e32, e64) == 6
+    e64[8] = e32[8]
+    assert at.fp64_threshold(e32, e64) == 99
+
+
+def test_autotune_bin_batches_fall_in_their_bins():
+    from paper_1401_6238_gb300 import autotune as at
+    for i, L in enumerate(at.BINS):
+        lo = at.BINS[i - 1] if i else 0
+        b = at.bin_batch(L, (3, 4, 5), 16, seed=L) or at.bin_batch(L, (2,), 16, seed=L)
+        d = b.orders * (b.dims - 1) + 1
+        assert len(b) == 16 and (d > lo).all() and (d <= L).all()

@@ -380,10 +380,12 @@ int max_len_for(int buffers, size_t csize) {
 void make_launches(std::vector<hk::RealJob>& jobs, std::vector<hk::RealLaunch>& launches, bool one_per_launch,
                    int single_buffers, int max_single_L) {
     // kind: 0 pair (three shared buffers), 1 single (two), 2 single with
-    // global scratch (shared memory holds only twiddles), 3 split single
-    // (two blocks of two buffers of L/2)
+    // global scratch (shared memory holds only twiddles), 4 / 5 split single
+    // on a cluster of four / two blocks (two buffers of L/4 / L/2 each)
     auto kind = [&](const hk::RealJob& j) {
-        return !j.single ? 0 : (j.split ? 3 : (j.P.L > max_single_L ? 2 : 1));
+        if (!j.single) return 0;
+        if (j.split) return j.split == 2 ? 4 : 5;
+        return j.P.L > max_single_L ? 2 : 1;
     };
     std::stable_sort(jobs.begin(), jobs.end(), [&](const hk::RealJob& a, const hk::RealJob& b) {
         if (kind(a) != kind(b)) return kind(a) < kind(b);
@@ -396,8 +398,8 @@ void make_launches(std::vector<hk::RealJob>& jobs, std::vector<hk::RealLaunch>& 
         lc.first = (int)i;
         lc.nthr = nthr_of(L0);
         lc.Lmax = L0;
-        lc.arrays = kind(jobs[i]) == 0 ? 3 : (kind(jobs[i]) == 1 ? single_buffers : (kind(jobs[i]) == 3 ? 2 : 0));
-        lc.split = kind(jobs[i]) == 3 ? 1 : 0;
+        lc.arrays = kind(jobs[i]) == 0 ? 3 : (kind(jobs[i]) == 1 ? single_buffers : (kind(jobs[i]) >= 3 ? 2 : 0));
+        lc.split = jobs[i].split;
         size_t j = i + 1;
         if (!one_per_launch)
             while (j < jobs.size() && nthr_of(jobs[j].P.L) == lc.nthr && kind(jobs[j]) == kind(jobs[i])) ++j;
@@ -445,6 +447,14 @@ int split_length(const hankel_plan_s* p, int L) {
     const int max_single_L = max_len_for(2, 2 * real_size(p->dtype));
     if (L % 2 != 0 || L / 2 > max_single_L || lengths().find(L / 2) == nullptr) return 0;
     return L / 2;
+}
+
+// Four-way split (a cluster of four blocks of length L/4, real_path.cu),
+// preferred to the two-way one where L/4 is a transform length: 0 if not.
+int split4_length(const hankel_plan_s* p, int L) {
+    const int max_single_L = max_len_for(2, 2 * real_size(p->dtype));
+    if (L % 4 != 0 || L / 4 > max_single_L || lengths().find(L / 4) == nullptr) return 0;
+    return L / 4;
 }
 
 // Pair jobs and work items of the persistent forward kernel for the tensors
@@ -650,14 +660,20 @@ hankel_status build_real_path(hankel_plan_s* p) {
         p->bwd_jobs.push_back(J);
     }
     // single jobs too long for one block's shared memory run as split jobs
-    // (two blocks of length L/2) where L/2 is a transform length of the plan
+    // on thread-block clusters: two blocks of length L/2 (split 3), else
+    // four of L/4 (split 2), where that is a transform length of the plan
     for (auto* v : {&p->fwd_jobs, &p->bwd_jobs})
         for (auto& J : *v) {
             const int L = J.P.L;
-            if (J.single && L > max_single_L && split_length(p, L) > 0) {
-                J.split = 1;
+            if (!J.single || L <= max_single_L) continue;
+            if (split_length(p, L) > 0) {
+                J.split = 3;
                 J.twL = p->tw_off.at(L);
                 J.P = fft_plan_of(p, L / 2);
+            } else if (split4_length(p, L) > 0) {
+                J.split = 2;
+                J.twL = p->tw_off.at(L);
+                J.P = fft_plan_of(p, L / 4);
             }
         }
     const bool opl = (p->flags & HANKEL_ONE_PER_LAUNCH) != 0;
@@ -1159,7 +1175,12 @@ hankel_status hankel_plan(hankel_plan_t* out, const hankel_desc* descs, int64_t 
         const int max_single_L = max_len_for(2, 2 * real_size(dtype));
         const size_t nL = Ls.size();
         for (size_t i = 0; i < nL; ++i)
-            if (Ls[i] > max_single_L && split_length(p, Ls[i]) > 0) Ls.push_back(Ls[i] / 2);
+            if (Ls[i] > max_single_L) {
+                if (split_length(p, Ls[i]) > 0)
+                    Ls.push_back(Ls[i] / 2);
+                else if (split4_length(p, Ls[i]) > 0)
+                    Ls.push_back(Ls[i] / 4);
+            }
         s = upload_twiddles(p, Ls);
         if (s == HANKEL_OK) s = build_real_path(p);
     } else {

@@ -29,17 +29,17 @@ inline void fill_magic(FftPlan& P) {
 // either a pair (A, B) of tensors with the same L -- two real problems share
 // every complex transform -- or a single tensor, whose h and x share one
 // transform as h + i x.
-// A single job may also be `split`: its length L = 2M exceeds what one block's
-// shared memory holds, so each length-L transform runs as two blocks, block
-// c computing the bins 2k + c by one length-M transform (decimation in
-// frequency); P is then the length-M plan and twL the offset of the
-// length-L twiddle table.
+// A single job may also be `split`: its length L exceeds what one block's
+// shared memory holds, so each length-L transform runs on a thread-block
+// cluster of s = 2 or 4 blocks, block c computing the bins s k + c by one
+// length-M transform, M = L/s (decimation in frequency); P is then the
+// length-M plan and twL the offset of the length-L twiddle table.
 struct RealJob {
     FftPlan P;
     int32_t single;
     int32_t mA, nA, dA, iA;
     int32_t mB, nB, dB, iB;
-    int32_t split, twL;
+    int32_t split, twL;  // split: 2 / 3 a cluster of four / two blocks (P: length L/4 / L/2)
     int64_t hA, xA, yA, hB, xB, yB;
     int64_t wsA, wsB;  // element offsets of each tensor's spectrum in the workspace
 };
@@ -75,7 +75,7 @@ struct FoldGroup {
 // Launch of one group of jobs that share a block size.
 struct RealLaunch {
     int32_t first, count;  // range in the job table
-    int32_t nthr, split, Lmax, arrays;  // split: the jobs are split jobs (two blocks each)
+    int32_t nthr, split, Lmax, arrays;  // split: the jobs' split (RealJob::split)
     int32_t fp64;  // nonzero: spectrum powers in FP64 (some tensor of the launch asks for them)
 };
 

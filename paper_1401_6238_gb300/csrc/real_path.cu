@@ -19,6 +19,7 @@
 // Both spectra are Hermitian; ifft(Q)[j] = fft(Q)[(L-j) mod L]/L, so one
 // forward transform of Q_h/L + i Q_x returns grad_h (real part, index
 // reversed) and grad_x (imaginary part).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -28,6 +29,8 @@
 
 #include "fft_stage.cuh"
 #include "launch.h"
+
+namespace cg = cooperative_groups;
 
 namespace hk {
 
@@ -567,28 +570,53 @@ __device__ __forceinline__ void dif_stage(cx<T>* buf, const Src& u, int M, int c
     }
 }
 
+// v_c[n] = w_L^{c n} sum_j u[n + j M] (-i)^{j c} (j, c < 4) into shared
+// memory, n < M = L/4: block c of a four-way split, whose length-M
+// transform gives the bins 4k + c of the length-L one.
+template <typename T, class Src>
+__device__ __forceinline__ void dif4_stage(cx<T>* buf, const Src& u, int M, int c, const TwTab<T>& twL,
+                                           const Group& g) {
+    // unrolled: the loads of several n in flight at once (they come from L2)
+#pragma unroll 4
+    for (int n = g.tid; n < M; n += g.nthr) {
+        const cx<T> a0 = u(n), a1 = u(n + M), a2 = u(n + 2 * M), a3 = u(n + 3 * M);
+        cx<T> v;
+        if (c == 0) {
+            v = (a0 + a2) + (a1 + a3);
+        } else if (c == 2) {
+            v = (a0 + a2) - (a1 + a3);
+        } else {
+            const cx<T> e = a0 - a2, o = a1 - a3;  // c = 1: e - i o; c = 3: e + i o
+            v = (c == 1) ? e + mul_ni(o) : e + mul_pi(o);
+        }
+        buf[sp(n)] = (c == 0) ? v : cmul(v, twL(c * n));
+    }
+}
+
+// Stores of a split job's block c: bin s k + c of the whole spectrum (s = 2
+// or 4 blocks per transform).
 template <typename T>
-struct SplitSt {  // complex bins 2k + c of a length-2M spectrum
+struct SplitSt {  // complex bins s k + c
     cx<T>* p;
-    int c;
-    __device__ __forceinline__ void operator()(int k, cx<T> v) const { p[2 * k + c] = v; }
+    int c, s;
+    __device__ __forceinline__ void operator()(int k, cx<T> v) const { p[s * k + c] = v; }
 };
 
 template <typename T>
-struct SplitRealSt {  // real part of the bins 2k + c, truncated to n
+struct SplitRealSt {  // real part of the bins s k + c, truncated to n
     T* y;
-    int n, c;
+    int n, c, s;
     __device__ __forceinline__ void operator()(int k, cx<T> v) const {
-        const int i = 2 * k + c;
+        const int i = s * k + c;
         if (i < n) y[i] = v.x;
     }
 };
 
 template <typename T>
-struct SplitAdjSt {  // AdjSt at the bins 2k + c
+struct SplitAdjSt {  // AdjSt at the bins s k + c
     AdjSt<T> st;
-    int c;
-    __device__ __forceinline__ void operator()(int k, cx<T> v) const { st(2 * k + c, v); }
+    int c, s;
+    __device__ __forceinline__ void operator()(int k, cx<T> v) const { st(s * k + c, v); }
 };
 
 // Shared-memory layout of the split kernels: twiddle tables of lengths M and
@@ -601,99 +629,121 @@ struct SplitSmem {
 
 template <typename T>
 __device__ __forceinline__ SplitSmem<T> split_smem(unsigned char* raw, const RealJob& J, const cx<T>* tw_all,
-                                                  int Mmax, const Group& g) {
+                                                  int Mmax, const Group& g, int ways = 2) {
     cx<T>* t0 = reinterpret_cast<cx<T>*>(raw + RED_BYTES);
     cx<T>* t1 = t0 + TW_SMEM;
     SplitSmem<T> s;
     s.twM = load_twiddles(t0, tw_all + J.P.tw_off, J.P.L, g);
-    s.twL = load_twiddles(t1, tw_all + J.twL, 2 * J.P.L, g);
+    s.twL = load_twiddles(t1, tw_all + J.twL, ways * J.P.L, g);
     s.b0 = t1 + TW_SMEM;
     s.b1 = s.b0 + smem_elems(Mmax);
     return s;
 }
 
-// Spectra of split jobs: block (job, source, c); sources (bit mask `srcs`):
-// bit 0 the packed input h~ + i x~ into the tensor's spectrum slot wsA,
-// bit 1 the upstream gradient g~ into the job's scratch wsB.
-template <typename T>
-__global__ void __launch_bounds__(512) split_spectrum_kernel(const RealJob* __restrict__ jobs, int first,
-                                                              const T* __restrict__ h, const T* __restrict__ x,
-                                                              const T* __restrict__ gy, int srcs, cx<T>* ws,
-                                                              const cx<T>* __restrict__ tw_all, int Mmax) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int nsrc = (srcs & 1) + ((srcs >> 1) & 1);
-    const int c = blockIdx.x & 1;
-    const int s_i = (blockIdx.x >> 1) % nsrc;
-    const int src = (nsrc == 2) ? s_i : ((srcs & 1) ? 0 : 1);
-    const RealJob J = jobs[first + (int)(blockIdx.x >> 1) / nsrc];
-    const Group g{(int)threadIdx.x, (int)blockDim.x, 0};
-    const SplitSmem<T> sm = split_smem(smem_raw, J, tw_all, Mmax, g);
-    const int M = J.P.L;
-    g.sync();
-    if (src == 0)
-        dif_stage(sm.b0, PairSrc<T>{h + J.hA, J.dA, x + J.xA, J.nA}, M, c, sm.twL, g);
+// Split jobs on thread-block clusters: the W = 2 or 4 blocks of one tensor
+// form a cluster (block c = rank in the cluster), each running a length-L/W
+// transform after a radix-W decimation-in-frequency stage, so that one
+// tensor occupies W SMs and the whole of a forward or adjoint product is one
+// launch.  The spectra pass between the two transforms
+// through the plan workspace (L2-resident): a cluster barrier (release /
+// acquire at cluster scope) makes each block's quarter of the spectrum
+// visible to the other three.  The blocks of a cluster run together, so the
+// barrier never waits on a block that has not started.
+
+template <int W, typename T, class Src>
+__device__ __forceinline__ void difw_stage(cx<T>* buf, const Src& u, int M, int c, const TwTab<T>& twL,
+                                           const Group& g) {
+    if constexpr (W == 4)
+        dif4_stage(buf, u, M, c, twL, g);
     else
-        dif_stage(sm.b0, PairSrc<T>{gy + J.yA, J.nA, nullptr, 0}, M, c, sm.twL, g);
-    g.sync();
-    cx<T>* dst = ws + (src == 0 ? J.wsA : J.wsB);
-    fft_stage<T>(J.P, GLd<T>{nullptr, 0, nullptr, 0}, sm.b0, sm.b1, sm.b0, SplitSt<T>{dst, c}, false, sm.twM, g);
+        dif_stage(buf, u, M, c, twL, g);
 }
 
-// y = fft(P)[0:n] and alpha for split jobs, from the spectra in wsA.
-template <typename T>
-__global__ void __launch_bounds__(512) split_forward_kernel(const RealJob* __restrict__ jobs, int first,
-                                                             T* __restrict__ y, T* __restrict__ alpha,
-                                                             const cx<T>* ws, const cx<T>* __restrict__ tw_all,
-                                                             int Mmax, int flags) {
+// y = fft(P)[0:n] and alpha: S = fft(h~ + i x~) into wsA, barrier, then the
+// product's transform.
+template <typename T, int W>
+__global__ void __cluster_dims__(W, 1, 1) __launch_bounds__(512)
+    cluster_forward_kernel(const RealJob* __restrict__ jobs, int first, const T* __restrict__ h,
+                           const T* __restrict__ x, T* __restrict__ y, T* __restrict__ alpha, cx<T>* ws,
+                           const cx<T>* __restrict__ tw_all, int Mmax, int flags) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* red = reinterpret_cast<double*>(smem_raw);
-    const int c = blockIdx.x & 1;
-    const RealJob J = jobs[first + (int)(blockIdx.x >> 1)];
+    cg::cluster_group cl = cg::this_cluster();
+    const int c = (int)cl.block_rank();
+    const RealJob J = jobs[first + (int)blockIdx.x / W];
     const Group g{(int)threadIdx.x, (int)blockDim.x, 0};
-    const SplitSmem<T> sm = split_smem(smem_raw, J, tw_all, Mmax, g);
-    const int M = J.P.L, L = 2 * M;
+    const SplitSmem<T> sm = split_smem(smem_raw, J, tw_all, Mmax, g, W);
+    const int M = J.P.L, L = W * M;
     const bool fp64 = (flags & HANKEL_FP64_POWER) != 0;
     const T invL = T(1) / T(L);
-    const cx<T>* S = ws + J.wsA;
+    cx<T>* S = ws + J.wsA;
     g.sync();
+    difw_stage<W>(sm.b0, PairSrc<T>{h + J.hA, J.dA, x + J.xA, J.nA}, M, c, sm.twL, g);
+    g.sync();
+    fft_stage<T>(J.P, GLd<T>{nullptr, 0, nullptr, 0}, sm.b0, sm.b1, sm.b0, SplitSt<T>{S, c, W}, false, sm.twM, g);
+    cl.sync();
     if (y != nullptr) {
-        dif_stage(sm.b0, ProductSrc<T>{S, L, J.mA, invL, fp64}, M, c, sm.twL, g);
+        difw_stage<W>(sm.b0, ProductSrc<T>{S, L, J.mA, invL, fp64}, M, c, sm.twL, g);
         g.sync();
-        fft_stage<T>(J.P, GLd<T>{nullptr, 0, nullptr, 0}, sm.b0, sm.b1, sm.b0, SplitRealSt<T>{y + J.yA, J.nA, c},
+        fft_stage<T>(J.P, GLd<T>{nullptr, 0, nullptr, 0}, sm.b0, sm.b1, sm.b0, SplitRealSt<T>{y + J.yA, J.nA, c, W},
                      false, sm.twM, g);
     }
-    if (alpha != nullptr && c == 0) {
+    if (alpha != nullptr) {
+        // each block sums 1/W of the bins 0 .. L/2; block 0 adds the other
+        // blocks' partial sums after a second barrier
         double aA = 0.0;
-        for (int k = g.tid; k <= L / 2; k += g.nthr) {
+        for (int k = c * g.nthr + g.tid; k <= L / 2; k += W * g.nthr) {
             const int kc = (k == 0) ? 0 : L - k;
             cx<T> Hk, Xk;
             unpack(S[k], conjg(S[kc]), Hk, Xk);
             aA += alpha_term(Hk, Xk, J.mA, invL, fp64, k, kc);
         }
         const double sA = group_sum(aA, red, g);
-        if (g.tid == 0) alpha[J.iA] = (T)sA;
+        // slots 33 .. 32 + W - 1 of block 0's reduction scratch (past group_sum's)
+        double* part = cl.map_shared_rank(red, 0);
+        if (g.tid == 0 && c != 0) part[32 + c] = sA;
+        cl.sync();
+        if (g.tid == 0 && c == 0) {
+            double t = sA;
+            for (int r = 1; r < W; ++r) t += red[32 + r];
+            alpha[J.iA] = (T)t;
+        }
     }
 }
 
-// Gradients of split jobs from U (wsA) and G (wsB).
-template <typename T>
-__global__ void __launch_bounds__(512) split_backward_kernel(const RealJob* __restrict__ jobs, int first,
-                                                              T* __restrict__ gh, T* __restrict__ gx, const cx<T>* ws,
-                                                              const cx<T>* __restrict__ tw_all, int Mmax,
-                                                              int flags) {
+// Gradients: G = fft(g~) into wsB (and U = fft(h~ + i x~) into wsA unless
+// kept from the forward), barrier, then the adjoint's transform.
+template <typename T, int W>
+__global__ void __cluster_dims__(W, 1, 1) __launch_bounds__(512)
+    cluster_backward_kernel(const RealJob* __restrict__ jobs, int first, const T* __restrict__ gy,
+                            const T* __restrict__ h, const T* __restrict__ x, T* __restrict__ gh, T* __restrict__ gx,
+                            cx<T>* ws, const cx<T>* __restrict__ tw_all, int Mmax, int flags, int stored) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int c = blockIdx.x & 1;
-    const RealJob J = jobs[first + (int)(blockIdx.x >> 1)];
+    cg::cluster_group cl = cg::this_cluster();
+    const int c = (int)cl.block_rank();
+    const RealJob J = jobs[first + (int)blockIdx.x / W];
     const Group g{(int)threadIdx.x, (int)blockDim.x, 0};
-    const SplitSmem<T> sm = split_smem(smem_raw, J, tw_all, Mmax, g);
-    const int M = J.P.L, L = 2 * M;
+    const SplitSmem<T> sm = split_smem(smem_raw, J, tw_all, Mmax, g, W);
+    const int M = J.P.L, L = W * M;
     const bool fp64 = (flags & HANKEL_FP64_POWER) != 0;
     const T invL = T(1) / T(L);
     g.sync();
-    dif_stage(sm.b0, AdjointSrc<T>{ws + J.wsA, ws + J.wsB, L, J.mA, invL, fp64}, M, c, sm.twL, g);
+    if (!stored) {
+        difw_stage<W>(sm.b0, PairSrc<T>{h + J.hA, J.dA, x + J.xA, J.nA}, M, c, sm.twL, g);
+        g.sync();
+        fft_stage<T>(J.P, GLd<T>{nullptr, 0, nullptr, 0}, sm.b0, sm.b1, sm.b0, SplitSt<T>{ws + J.wsA, c, W}, false,
+                     sm.twM, g);
+        g.sync();
+    }
+    difw_stage<W>(sm.b0, PairSrc<T>{gy + J.yA, J.nA, nullptr, 0}, M, c, sm.twL, g);
+    g.sync();
+    fft_stage<T>(J.P, GLd<T>{nullptr, 0, nullptr, 0}, sm.b0, sm.b1, sm.b0, SplitSt<T>{ws + J.wsB, c, W}, false,
+                 sm.twM, g);
+    cl.sync();
+    difw_stage<W>(sm.b0, AdjointSrc<T>{ws + J.wsA, ws + J.wsB, L, J.mA, invL, fp64}, M, c, sm.twL, g);
     g.sync();
     const AdjSt<T> st{gh ? gh + J.hA : nullptr, J.dA, gx ? gx + J.xA : nullptr, J.nA, L};
-    fft_stage<T>(J.P, GLd<T>{nullptr, 0, nullptr, 0}, sm.b0, sm.b1, sm.b0, SplitAdjSt<T>{st, c}, false, sm.twM, g);
+    fft_stage<T>(J.P, GLd<T>{nullptr, 0, nullptr, 0}, sm.b0, sm.b1, sm.b0, SplitAdjSt<T>{st, c, W}, false, sm.twM, g);
 }
 
 // ------------------------------------------------ anti-circulant expansion
@@ -818,28 +868,15 @@ static size_t split_smem_bytes(const RealLaunch& lc) {
 }
 
 template <typename T>
-static cudaError_t launch_split_spectra(const RealLaunch& lc, const RealJob* jobs, const void* h, const void* x,
-                                        const void* gy, int srcs, const void* tw, void* ws, cudaStream_t st) {
-    const size_t smem = split_smem_bytes<T>(lc);
-    auto k = split_spectrum_kernel<T>;
-    cudaError_t e = ensure_smem(k, smem);
-    if (e != cudaSuccess) return e;
-    const int nsrc = (srcs & 1) + ((srcs >> 1) & 1);
-    k<<<lc.count * 2 * nsrc, lc.nthr, smem, st>>>(jobs, lc.first, (const T*)h, (const T*)x, (const T*)gy, srcs,
-                                                   (cx<T>*)ws, (const cx<T>*)tw, lc.Lmax);
-    return cudaGetLastError();
-}
-
-template <typename T>
 static cudaError_t launch_fwd_t(const RealLaunch& lc, const RealJob* jobs, const void* h, const void* x, void* y,
                                 void* alpha, const void* tw, void* ws, int flags, cudaStream_t st) {
-    if (lc.split) {
-        cudaError_t e = launch_split_spectra<T>(lc, jobs, h, x, nullptr, 1, tw, ws, st);
-        if (e != cudaSuccess) return e;
+    if (lc.split >= 2) {  // a cluster of W blocks per job
+        const int W = lc.split == 2 ? 4 : 2;
         const size_t smem = split_smem_bytes<T>(lc);
-        auto k = split_forward_kernel<T>;
-        if ((e = ensure_smem(k, smem)) != cudaSuccess) return e;
-        k<<<lc.count * 2, lc.nthr, smem, st>>>(jobs, lc.first, (T*)y, (T*)alpha, (const cx<T>*)ws,
+        auto k = W == 4 ? cluster_forward_kernel<T, 4> : cluster_forward_kernel<T, 2>;
+        cudaError_t e = ensure_smem(k, smem);
+        if (e != cudaSuccess) return e;
+        k<<<lc.count * W, lc.nthr, smem, st>>>(jobs, lc.first, (const T*)h, (const T*)x, (T*)y, (T*)alpha, (cx<T>*)ws,
                                                 (const cx<T>*)tw, lc.Lmax, flags);
         return cudaGetLastError();
     }
@@ -861,14 +898,14 @@ template <typename T>
 static cudaError_t launch_bwd_t(const RealLaunch& lc, const RealJob* jobs, const void* gy, const void* h,
                                 const void* x, void* gh, void* gx, const void* tw, void* ws, int flags, int stored,
                                 cudaStream_t st) {
-    if (lc.split) {
-        cudaError_t e = launch_split_spectra<T>(lc, jobs, h, x, gy, stored ? 2 : 3, tw, ws, st);
-        if (e != cudaSuccess) return e;
+    if (lc.split >= 2) {  // a cluster of W blocks per job
+        const int W = lc.split == 2 ? 4 : 2;
         const size_t smem = split_smem_bytes<T>(lc);
-        auto k = split_backward_kernel<T>;
-        if ((e = ensure_smem(k, smem)) != cudaSuccess) return e;
-        k<<<lc.count * 2, lc.nthr, smem, st>>>(jobs, lc.first, (T*)gh, (T*)gx, (const cx<T>*)ws, (const cx<T>*)tw,
-                                                lc.Lmax, flags);
+        auto k = W == 4 ? cluster_backward_kernel<T, 4> : cluster_backward_kernel<T, 2>;
+        cudaError_t e = ensure_smem(k, smem);
+        if (e != cudaSuccess) return e;
+        k<<<lc.count * W, lc.nthr, smem, st>>>(jobs, lc.first, (const T*)gy, (const T*)h, (const T*)x, (T*)gh, (T*)gx,
+                                                (cx<T>*)ws, (const cx<T>*)tw, lc.Lmax, flags, stored);
         return cudaGetLastError();
     }
     const size_t smem = real_smem_bytes<T>(lc);

@@ -97,25 +97,28 @@ __device__ __forceinline__ void unpack(cx<T> u, cx<T> w_conj, cx<T>& a, cx<T>& b
 }
 
 // Spectral product of one tensor at bin k: P = ifft(h~)_k X_k^{m-1}, plus the
-// alpha term ifft(h~)_k X_k^m; formed in A precision.
+// alpha term ifft(h~)_k X_k^m; formed in A precision, the alpha term rounded
+// to the data type T (summed in T per thread: FP64 instructions hold this
+// GPU's narrow FP64 pipe for many cycles, and FP32 data carry FP32 rounding
+// already).
 template <typename A, typename T>
-__device__ __forceinline__ cx<T> product(cx<T> Hk, cx<T> Xk, int m, T invL, double& aterm, bool want_alpha = true) {
+__device__ __forceinline__ cx<T> product(cx<T> Hk, cx<T> Xk, int m, T invL, T& aterm, bool want_alpha = true) {
     const cx<A> hh = scal(up<A>(conjg(Hk)), (A)invL);
     const cx<A> X = up<A>(Xk);
     const cx<A> p = times_pow(hh, X, m - 1);
-    aterm = want_alpha ? (double)cmul(p, X).x : 0.0;
+    if (want_alpha) aterm = (T)cmul(p, X).x;
     return mk<T>((T)p.x, (T)p.y);
 }
 
 // Alpha contribution of bins k and L-k (their terms are complex conjugates).
 template <typename T>
-__device__ __forceinline__ double alpha_term(cx<T> Hk, cx<T> Xk, int m, T invL, bool fp64, int k, int kc) {
-    double at;
+__device__ __forceinline__ T alpha_term(cx<T> Hk, cx<T> Xk, int m, T invL, bool fp64, int k, int kc) {
+    T at = T(0);
     if (fp64)
         product<double>(Hk, Xk, m, invL, at);
     else
         product<T>(Hk, Xk, m, invL, at);
-    return (k == kc) ? at : 2.0 * at;
+    return (k == kc) ? at : T(2) * at;
 }
 
 template <typename T>
@@ -138,7 +141,7 @@ __global__ void __launch_bounds__(512) real_fwd_kernel(const RealJob* __restrict
     const bool fp64 = (flags & HANKEL_FP64_POWER) != 0;
     const T invL = T(1) / T(L);
     const PairSt<T> store{y + J.yA, J.nA, y + J.yB, J.single ? 0 : J.nB};
-    double aA = 0.0, aB = 0.0;
+    T aA = T(0), aB = T(0);
     cx<T>*S1, *F, *O;
 
     g.sync();
@@ -152,11 +155,11 @@ __global__ void __launch_bounds__(512) real_fwd_kernel(const RealJob* __restrict
             const int kc = (k == 0) ? 0 : L - k;
             cx<T> Hk, Xk;
             unpack(S1[sp(k)], conjg(S1[sp(kc)]), Hk, Xk);
-            double at;
+            T at = T(0);
             const bool wa = alpha != nullptr;
             const cx<T> Pk =
                 fp64 ? product<double>(Hk, Xk, J.mA, invL, at, wa) : product<T>(Hk, Xk, J.mA, invL, at, wa);
-            if (wa) aA += (k == kc) ? at : 2.0 * at;
+            if (wa) aA += (k == kc) ? at : T(2) * at;
             F[sp(k)] = Pk;
             if (kc != k) F[sp(kc)] = conjg(Pk);
         }
@@ -181,7 +184,7 @@ __global__ void __launch_bounds__(512) real_fwd_kernel(const RealJob* __restrict
             cx<T> HA, HB, XA, XB;
             unpack(S1[sp(k)], conjg(S1[sp(kc)]), HA, HB);
             unpack(S2[sp(k)], conjg(S2[sp(kc)]), XA, XB);
-            double atA, atB;
+            T atA = T(0), atB = T(0);
             cx<T> PA, PB;
             const bool wa = alpha != nullptr;
             if (fp64) {
@@ -192,8 +195,8 @@ __global__ void __launch_bounds__(512) real_fwd_kernel(const RealJob* __restrict
                 PB = product<T>(HB, XB, J.mB, invL, atB, wa);
             }
             if (wa) {
-                aA += (k == kc) ? atA : 2.0 * atA;
-                aB += (k == kc) ? atB : 2.0 * atB;
+                aA += (k == kc) ? atA : T(2) * atA;
+                aB += (k == kc) ? atB : T(2) * atB;
             }
             F[sp(k)] = PA + mul_pi(PB);
             if (kc != k) F[sp(kc)] = conjg(PA) + mul_pi(conjg(PB));
@@ -203,8 +206,8 @@ __global__ void __launch_bounds__(512) real_fwd_kernel(const RealJob* __restrict
     g.sync();
     if (y != nullptr) fft_stage<T>(P, GLd<T>{nullptr, 0, nullptr, 0}, F, O, F, store, false, tw, g);
     if (alpha != nullptr) {
-        const double sA = group_sum(aA, red, g);
-        const double sB = J.single ? 0.0 : group_sum(aB, red, g);
+        const double sA = group_sum((double)aA, red, g);
+        const double sB = J.single ? 0.0 : group_sum((double)aB, red, g);
         if (g.tid == 0) {
             alpha[J.iA] = (T)sA;
             if (!J.single && J.iB >= 0) alpha[J.iB] = (T)sB;
@@ -294,13 +297,13 @@ __global__ void __launch_bounds__(512) real_multi_kernel(const MultiJob* __restr
         // alpha = sum_k P_k X_{1,k}: bins k and L - k contribute complex conjugates
         S = fft_stage<T>(P, GLd<T>{x + J.xA[0], J.nA[0], two ? x + J.xB[0] : nullptr, two ? J.nB[0] : 0}, nullptr,
                          bA, bB, keep_st, true, tw, g);
-        double aA = 0.0, aB = 0.0;
+        T aA = T(0), aB = T(0);
         for (int k = g.tid; k <= L / 2; k += g.nthr) {
             const int kc = (k == 0) ? 0 : L - k;
             cx<T> XA, XB;
             unpack(S[sp(k)], conjg(S[sp(kc)]), XA, XB);
-            // terms in T precision, summed in FP64 (one conversion and one
-            // FP64 add per term: FP64 arithmetic is slow on this part)
+            // terms and each thread's sums in T precision; FP64 only for the
+            // sum over the block (FP64 arithmetic is slow on this part)
             T tA, tB;
             if (kc == k) {
                 const cx<T> v = acc[sp(k)];
@@ -311,11 +314,11 @@ __global__ void __launch_bounds__(512) real_multi_kernel(const MultiJob* __restr
                 tA = T(2) * (PA.x * XA.x - PA.y * XA.y);
                 tB = T(2) * (PB.x * XB.x - PB.y * XB.y);
             }
-            aA += (double)tA;
-            aB += (double)tB;
+            aA += tA;
+            aB += tB;
         }
-        const double sA = group_sum(aA, red, g);
-        const double sB = two ? group_sum(aB, red, g) : 0.0;
+        const double sA = group_sum((double)aA, red, g);
+        const double sB = two ? group_sum((double)aB, red, g) : 0.0;
         if (g.tid == 0) {
             alpha[J.iA] = (T)sA;
             if (two) alpha[J.iB] = (T)sB;
@@ -455,15 +458,15 @@ __global__ void __launch_bounds__(512) real_fwd_global_kernel(const RealJob* __r
     cx<T>* F = (S == W0) ? W1 : W0;
     if (flags & HANKEL_STORE_SPECTRA)
         for (int k = g.tid; k < L; k += g.nthr) ws[J.wsA + k] = S[k];
-    double aA = 0.0;
+    T aA = T(0);
     const bool wa = alpha != nullptr;
     for (int k = g.tid; k <= L / 2; k += g.nthr) {
         const int kc = (k == 0) ? 0 : L - k;
         cx<T> Hk, Xk;
         unpack(S[k], conjg(S[kc]), Hk, Xk);
-        double at;
+        T at = T(0);
         const cx<T> Pk = fp64 ? product<double>(Hk, Xk, J.mA, invL, at, wa) : product<T>(Hk, Xk, J.mA, invL, at, wa);
-        if (wa) aA += (k == kc) ? at : 2.0 * at;
+        if (wa) aA += (k == kc) ? at : T(2) * at;
         F[k] = Pk;
         if (kc != k) F[kc] = conjg(Pk);
     }
@@ -471,7 +474,7 @@ __global__ void __launch_bounds__(512) real_fwd_global_kernel(const RealJob* __r
     g.sync();
     if (y != nullptr) fft_global<T>(P, GLd<T>{nullptr, 0, nullptr, 0}, F, S, F, store, false, tw, g);
     if (wa) {
-        const double sA = group_sum(aA, red, g);
+        const double sA = group_sum((double)aA, red, g);
         if (g.tid == 0) alpha[J.iA] = (T)sA;
     }
 }
@@ -540,7 +543,7 @@ struct ProductSrc {
         const int kc = (k == 0) ? 0 : L - k;
         cx<T> Hk, Xk;
         unpack(S[k], conjg(S[kc]), Hk, Xk);
-        double at;
+        T at;
         return fp64 ? product<double>(Hk, Xk, m, invL, at, false) : product<T>(Hk, Xk, m, invL, at, false);
     }
 };
@@ -691,14 +694,14 @@ __global__ void __cluster_dims__(W, 1, 1) __launch_bounds__(512)
     if (alpha != nullptr) {
         // each block sums 1/W of the bins 0 .. L/2; block 0 adds the other
         // blocks' partial sums after a second barrier
-        double aA = 0.0;
+        T aA = T(0);
         for (int k = c * g.nthr + g.tid; k <= L / 2; k += W * g.nthr) {
             const int kc = (k == 0) ? 0 : L - k;
             cx<T> Hk, Xk;
             unpack(S[k], conjg(S[kc]), Hk, Xk);
             aA += alpha_term(Hk, Xk, J.mA, invL, fp64, k, kc);
         }
-        const double sA = group_sum(aA, red, g);
+        const double sA = group_sum((double)aA, red, g);
         // slots 33 .. 32 + W - 1 of block 0's reduction scratch (past group_sum's)
         double* part = cl.map_shared_rank(red, 0);
         if (g.tid == 0 && c != 0) part[32 + c] = sA;

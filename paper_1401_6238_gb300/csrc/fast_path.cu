@@ -383,6 +383,9 @@ struct Params {
     float* alpha;
     int* ctr;
     cx<float>* slab;  // L = 5120: R BLOCK complex values per block
+    const float* gy;  // adjoint: upstream gradients (laid out as y) and outputs
+    float* gh;
+    float* gx;
     int nitems;
     int after;  // the item after the next one (claimed during the current item)
 };
@@ -623,6 +626,241 @@ __global__ void __launch_bounds__(BLOCK, HK_FAST_MIN_BLOCKS)
     }
 }
 
+// ------------------------------------------------------------ the adjoint
+
+// Gradients of a real loss through y = H x^{m-1} (the adjoint of the
+// product: with G = fft(g~), Q_k = G_k X_k^{m-1} / L + i (m-1) ifft(h~)_k
+// G_k X_k^{m-2}, and fft(Q) holds grad_h, index reversed, in its real part
+// and grad_x in its imaginary part).  Pair job (A, B) of one length: G =
+// fft(g~_A + i g~_B) once, its bins kept in the thread-private slab; then per
+// tensor U = fft(h~ + i x~), whose last pass leaves U on the thread's bins in
+// registers and the mirror bins with the partner lane as in the forward
+// kernel, G_A / G_B unpacked from the slab (the mirror bins' slots are read
+// from the partner thread's slab), Q formed in registers and transformed,
+// its first pass (radix R, no twiddles) from the same registers.  Five
+// transforms per pair, spectra never leave the block.
+template <int L>
+__device__ __noinline__ int run_adj_item(int first, int staged, int next) {
+    constexpr int R = rlast(L), T = nthr(L), Q = L / R, GS = gslots(L);
+    constexpr int QA = q0(Q), QB = q1(Q);
+    constexpr int H = (T < 32 ? T : 32) / 2;
+    constexpr int NBL = L / QA;
+    constexpr int IT = (NBL + T - 1) / T;
+    static_assert(BLOCK % T == 0, "a block holds whole groups");
+    const Params& c = fp_par;
+    const Tw tw;
+    const int g = threadIdx.x / T, t = threadIdx.x % T;
+    const FastJob& J = c.jobs[first + g];
+    auto buf = [&](int i) { return sm_bufL<L>(i) + g * GS; };
+    const int b = last_b<T>(t);
+    const bool self0 = b == 0, selfh = b == T / 2;
+    const int lane = threadIdx.x & 31, src = selfh ? lane : (lane ^ H);
+    // the slab: G on the thread's bins, slot s at gs[s * BLOCK]; the mirror
+    // bin of slot s is slot R-1-s of the partner thread (slot (R-s) mod R of
+    // this thread for butterfly 0, slot R-1-s of this thread for NB/2)
+    cx<float>* const slab = (L == LONG ? c.slab + (size_t)blockIdx.x * R * BLOCK : sm_stash());
+    cx<float>* const gs = slab + threadIdx.x;
+    const cx<float>* const gp = slab + ((self0 || selfh) ? threadIdx.x : (threadIdx.x ^ H));
+    int after = 0;
+    if (threadIdx.x == 0) after = atomicAdd(c.ctr + 2, 1) + (int)gridDim.x;  // stored at the end
+    const float invL = 1.0f / (float)L;
+    cx<float> v[R], q[R];
+
+    int cur = staged;
+    if (cur < 0) {
+        cur = 1;
+        stage<L, T>(buf(cur), c.gy + J.yA, J.nA, c.gy + J.yB, J.nB, t);
+        stage_wait();
+        gsync<T>(g);
+    }
+    // G = fft(g~_A + i g~_B) into the slab; A's inputs stream in meanwhile
+    first_pass<L, QA, T>(buf(cur), buf(cur ^ 1), t);
+    gsync<T>(g);
+    cur ^= 1;
+    if constexpr (QB > 1) {
+        seq_pass<L, QB, QA, T>(buf(cur), buf(cur ^ 1), t, tw);
+        gsync<T>(g);
+        cur ^= 1;
+    }
+    stage<L, T>(buf(cur ^ 1), c.h + J.hA, J.dA, c.x + J.xA, J.nA, t);
+    last_pass<L, R>(v, buf(cur), b, tw);
+#pragma unroll
+    for (int s = 0; s < R; ++s) gs[s * BLOCK] = v[s];
+    stage_wait();
+    gsync<T>(g);  // the slab and A's inputs are complete
+    cur ^= 1;
+
+    int staged_next = -1;
+#pragma unroll 1
+    for (int tensor = 0; tensor < 2; ++tensor) {
+        // (a missing partner or a padding slot runs on zeros and stores
+        // nothing: groups narrower than a warp share it, and every lane of a
+        // warp must reach the same shuffles)
+        const bool B = tensor == 1;
+        const int m = B ? J.mB : J.mA;
+        // U = fft(h~ + i x~)
+        first_pass<L, QA, T>(buf(cur), buf(cur ^ 1), t);
+        gsync<T>(g);
+        cur ^= 1;
+        if constexpr (QB > 1) {
+            seq_pass<L, QB, QA, T>(buf(cur), buf(cur ^ 1), t, tw);
+            gsync<T>(g);
+            cur ^= 1;
+        }
+        last_pass<L, R>(v, buf(cur), b, tw);
+        // Q on the thread's bins
+        cx<float> prev = v[0];
+#pragma unroll
+        for (int s = 0; s < R; ++s) {
+            const cx<float> o = v[R - 1 - s];
+            cx<float> uc = mk<float>(__shfl_sync(0xffffffffu, o.x, src), __shfl_sync(0xffffffffu, o.y, src));
+            uc = sel(self0, prev, uc);  // U_{L-k}
+            prev = o;
+            const cx<float> a = v[s];
+            // H = (U_k + conj U_{L-k}) / 2, X = -i (U_k - conj U_{L-k}) / 2
+            const cx<float> Hk = mk<float>(0.5f * (a.x + uc.x), 0.5f * (a.y - uc.y));
+            const cx<float> X = mk<float>(0.5f * (a.y + uc.y), 0.5f * (uc.x - a.x));
+            const cx<float> Gk = gs[s * BLOCK];
+            const cx<float> Gc = gp[(self0 ? (R - s) % R : R - 1 - s) * BLOCK];  // G_{L-k}
+            // G_A = (G_k + conj G_{L-k}) / 2, G_B = -i (G_k - conj G_{L-k}) / 2
+            const cx<float> Gt = B ? mk<float>(0.5f * (Gk.y + Gc.y), 0.5f * (Gc.x - Gk.x))
+                                   : mk<float>(0.5f * (Gk.x + Gc.x), 0.5f * (Gk.y - Gc.y));
+            cx<float> gx2 = Gt;  // G X^{m-2}
+            const int e = m - 2;
+            if (e & 1) gx2 = cmul(gx2, X);
+            if (e & 6) {
+                const cx<float> X2 = cmul(X, X);
+                if (e & 2) gx2 = cmul(gx2, X2);
+                if (e & 4) gx2 = cmul(gx2, cmul(X2, X2));
+            }
+            const cx<float> qh = cmul(gx2, X);                                        // G X^{m-1}
+            const cx<float> qx = cmul(mk<float>(Hk.x, -Hk.y), gx2);                   // conj(H) G X^{m-2}
+            const float fm = (float)(m - 1) * invL;
+            q[s] = mk<float>(qh.x * invL - qx.y * fm, qh.y * invL + qx.x * fm);      // qh / L + i (m-1) qx / L
+        }
+        // fft(Q): first pass from registers, the power-of-two passes, the last
+        // one storing the gradients
+        dft<R>(q);
+        sstore<R, 1>(buf(cur ^ 1), b * R, q);
+        gsync<T>(g);
+        cur ^= 1;
+        if constexpr (QB > 1) {
+            seq_pass<L, QB, R, T>(buf(cur), buf(cur ^ 1), t, tw);
+            gsync<T>(g);
+            cur ^= 1;
+        }
+        // the free buffer takes B's inputs, or after B the block's next item's
+        // upstream gradients when it has this length
+        if (!B) {
+            stage<L, T>(buf(cur ^ 1), c.h + J.hB, J.dB, c.x + J.xB, J.nB, t);
+        } else if (next < c.nitems) {
+            const FastItem N = c.items[next];
+            if (N.L == L) {
+                const FastJob& K = c.jobs[N.first + g];
+                staged_next = cur ^ 1;
+                stage<L, T>(buf(staged_next), c.gy + K.yA, K.nA, c.gy + K.yB, K.nB, t);
+            }
+        }
+        const int n = B ? J.nB : J.nA, d = B ? J.dB : J.dA;
+        float* gh = c.gh ? c.gh + (B ? J.hB : J.hA) : nullptr;
+        float* gx = c.gx ? c.gx + (B ? J.xB : J.xA) : nullptr;
+#pragma unroll 1
+        for (int j = 0; j < IT; ++j) {
+            const int bl = t + T * j;
+            if (IT * T == NBL || bl < NBL) {
+                cx<float> w[QA];
+                last_pass<L, QA>(w, buf(cur), bl, tw);
+#pragma unroll
+                for (int s = 0; s < QA; ++s) {
+                    const int i0 = bl + s * NBL;
+                    const int jh = i0 == 0 ? 0 : L - i0;
+                    if (gh != nullptr && jh < d) gh[jh] = w[s].x;
+                    if (gx != nullptr && i0 < n) gx[i0] = w[s].y;
+                }
+            }
+        }
+        if (!B) {
+            stage_wait();
+            gsync<T>(g);  // B's inputs are complete; the buffers are free
+            cur ^= 1;
+        }
+    }
+    if (threadIdx.x == 0) fp_par.after = after;
+    return staged_next;
+}
+
+__global__ void __launch_bounds__(BLOCK, HK_FAST_MIN_BLOCKS)
+    fast_bwd_kernel(const FastItem* __restrict__ items, int nitems, const FastJob* __restrict__ jobs,
+                    const float* __restrict__ gy, const float* __restrict__ h, const float* __restrict__ x,
+                    float* __restrict__ gh, float* __restrict__ gx, const cx<float>* __restrict__ tw2,
+                    const cx<float>* __restrict__ tw3, const cx<float>* __restrict__ tw5, cx<float>* slab,
+                    int* ctr) {
+    cx<float>* t2 = sm_t2();
+    cx<float>* t3 = sm_t3();
+    cx<float>* t5 = sm_t5();
+    for (int i = threadIdx.x; i < TW2; i += BLOCK) t2[i] = ldg_cx(tw2 + i);
+    for (int i = threadIdx.x; i < TW3; i += BLOCK) t3[i] = ldg_cx(tw3 + i);
+    for (int i = threadIdx.x; i < TW5; i += BLOCK) t5[i] = ldg_cx(tw5 + i);
+    if (threadIdx.x == 0) {
+        fp_par.items = items;
+        fp_par.jobs = jobs;
+        fp_par.h = h;
+        fp_par.x = x;
+        fp_par.y = nullptr;
+        fp_par.alpha = nullptr;
+        fp_par.ctr = ctr;
+        fp_par.slab = slab;
+        fp_par.gy = gy;
+        fp_par.gh = gh;
+        fp_par.gx = gx;
+        fp_par.nitems = nitems;
+        // items: blockIdx.x first, then claimed from the adjoint's counter
+        // (ctr[2], ctr[3]); the claim of the item after the next one
+        // overlaps the current item
+        fp_par.after = atomicAdd(ctr + 2, 1) + (int)gridDim.x;
+    }
+    __syncthreads();
+    int it = blockIdx.x, next = fp_par.after;
+    int staged = -1;
+    __syncthreads();
+    while (it < nitems) {
+        const FastItem I = items[it];
+        switch (I.L) {
+            case 5120: staged = run_adj_item<5120>(I.first, staged, next); break;
+            case 4096: staged = run_adj_item<4096>(I.first, staged, next); break;
+            case 3072: staged = run_adj_item<3072>(I.first, staged, next); break;
+            case 2048: staged = run_adj_item<2048>(I.first, staged, next); break;
+            case 1536: staged = run_adj_item<1536>(I.first, staged, next); break;
+            case 1024: staged = run_adj_item<1024>(I.first, staged, next); break;
+            case 768: staged = run_adj_item<768>(I.first, staged, next); break;
+            case 512: staged = run_adj_item<512>(I.first, staged, next); break;
+            case 384: staged = run_adj_item<384>(I.first, staged, next); break;
+            case 256: staged = run_adj_item<256>(I.first, staged, next); break;
+            case 192: staged = run_adj_item<192>(I.first, staged, next); break;
+            case 128: staged = run_adj_item<128>(I.first, staged, next); break;
+            case 96: staged = run_adj_item<96>(I.first, staged, next); break;
+            case 64: staged = run_adj_item<64>(I.first, staged, next); break;
+            case 48: staged = run_adj_item<48>(I.first, staged, next); break;
+            case 32: staged = run_adj_item<32>(I.first, staged, next); break;
+            default: staged = -1; break;
+        }
+        if (staged >= 0) stage_wait();
+        __syncthreads();
+        it = next;
+        next = fp_par.after;
+        __syncthreads();
+    }
+    // the last block to finish re-arms the adjoint's counter
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(ctr + 3, 1) == (int)gridDim.x - 1) {
+            ctr[2] = 0;
+            ctr[3] = 0;
+            __threadfence();
+        }
+    }
+}
+
 }  // namespace fp
 
 bool fast_length_ok(int L) {
@@ -690,5 +928,36 @@ cudaError_t launch_fast_forward(const FastItem* items, int nitems, int grid, con
 }
 
 int fast_blocks_per_sm() { return HK_FAST_MIN_BLOCKS; }
+
+cudaError_t launch_fast_backward(const FastItem* items, int nitems, int grid, const FastJob* jobs, const void* gy,
+                                 const void* h, const void* x, void* gh, void* gx, const void* t2, const void* t3,
+                                 const void* t5, void* slab, int* ctr, cudaStream_t st) {
+    const size_t smem = fast_smem_bytes();
+    auto k = fp::fast_bwd_kernel;
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (dev < 64 && !done[dev]) {
+            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            int maxsm = 0;
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+            if (e == cudaSuccess && maxsm > 0) {
+                const size_t want = (size_t)HK_FAST_MIN_BLOCKS * (smem + 1024);
+                const int pct = (int)std::min<size_t>(100, (want * 100 + maxsm - 1) / maxsm);
+                e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+            }
+            if (e != cudaSuccess) return e;
+            done[dev] = true;
+        }
+    }
+    k<<<grid, fp::BLOCK, smem, st>>>(items, nitems, jobs, (const float*)gy, (const float*)h, (const float*)x,
+                                     (float*)gh, (float*)gx, (const cx<float>*)t2, (const cx<float>*)t3,
+                                     (const cx<float>*)t5, (cx<float>*)slab, ctr);
+    return cudaGetLastError();
+}
 
 }  // namespace hk

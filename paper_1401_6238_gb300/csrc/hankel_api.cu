@@ -216,6 +216,7 @@ struct hankel_plan_s {
     int fast_grid = 0;
     int64_t fast_pairs = 0;  // pair jobs with at least one tensor (the rest pad items)
     bool fast_f64 = false;   // some job of the persistent launch asks for FP64 powers
+    bool fast_bwd = false;   // the adjoint of the persistent launch's tensors is persistent too
     int64_t fp64_tensors = 0;  // tensors whose spectrum power is formed in FP64
     // general path (complex data, distinct vectors, BHHB)
     hk::GeneralPlan* gen = nullptr;
@@ -524,7 +525,8 @@ hankel_status build_fast(hankel_plan_s* p, const std::vector<char>& sel, const s
         return cuda_fail(e, "cudaMalloc(jobs)");
     if ((e = cudaMalloc(&p->d_fast_items, p->fast_items.size() * sizeof(hk::FastItem))) != cudaSuccess)
         return cuda_fail(e, "cudaMalloc(jobs)");
-    if ((e = cudaMalloc(&p->d_fast_ctr, 2 * sizeof(int))) != cudaSuccess) return cuda_fail(e, "cudaMalloc(counter)");
+    // work counters: [0], [1] the forward's, [2], [3] the adjoint's
+    if ((e = cudaMalloc(&p->d_fast_ctr, 4 * sizeof(int))) != cudaSuccess) return cuda_fail(e, "cudaMalloc(counter)");
     // items are longest first: the first one's length sizes the slab
     const size_t slab = hk::fast_slab_bytes(p->fast_items.front().L);
     if (slab > 0 && (e = cudaMalloc(&p->d_fast_slab, slab * p->fast_grid)) != cudaSuccess)
@@ -546,7 +548,7 @@ hankel_status build_fast(hankel_plan_s* p, const std::vector<char>& sel, const s
     if (e == cudaSuccess)
         e = cudaMemcpy(p->d_fast_items, p->fast_items.data(), p->fast_items.size() * sizeof(hk::FastItem),
                        cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(p->d_fast_ctr, 0, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(p->d_fast_ctr, 0, 4 * sizeof(int));
     if (e == cudaSuccess) e = hk::launch_stage_twiddles(false, p->d_fast_tw, P2, 0);
     if (e == cudaSuccess) e = hk::launch_stage_twiddles(false, (char*)p->d_fast_tw + p->fast_tw3, P3, 0);
     if (e == cudaSuccess) e = hk::launch_stage_twiddles(false, (char*)p->d_fast_tw + p->fast_tw5, P5, 0);
@@ -613,6 +615,15 @@ hankel_status build_real_path(hankel_plan_s* p) {
     std::vector<int64_t> fwd_order;
     for (int64_t a : order)
         if (!on_fast[a]) fwd_order.push_back(a);
+    // the adjoint of the persistent launch's tensors runs persistent too,
+    // unless some of them share storage (their gradients are sums: the
+    // general path) or ask for FP64 spectrum powers
+    bool any_fast = false, fast64 = false;
+    for (int64_t i = 0; i < count; ++i) {
+        any_fast = any_fast || on_fast[i];
+        fast64 = fast64 || (on_fast[i] && want64[i]);
+    }
+    p->fast_bwd = any_fast && !fast64 && !p->shared_io;
     for (size_t k = 0; k < fwd_order.size();) {
         const std::vector<int64_t>& order = fwd_order;
         hk::RealJob J;
@@ -640,6 +651,12 @@ hankel_status build_real_path(hankel_plan_s* p) {
     // adjoint: tensors of one length in pairs that share the transform of
     // their upstream gradients (three shared buffers), longer ones alone
     const bool pair_bwd = (p->flags & HANKEL_ONE_PER_LAUNCH) == 0;
+    if (p->fast_bwd) {
+        std::vector<int64_t> rest;
+        for (int64_t a : order)
+            if (!on_fast[a]) rest.push_back(a);
+        order.swap(rest);
+    }
     for (size_t k = 0; k < order.size();) {
         hk::RealJob J;
         std::memset(&J, 0, sizeof(J));
@@ -713,6 +730,35 @@ hankel_status build_real_path(hankel_plan_s* p) {
     p->ws_bytes = (size_t)std::max<int64_t>(ws, 1) * 2 * real_size(p->dtype);
     e = cudaMalloc(&p->d_ws, p->ws_bytes);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(workspace)");
+    return HANKEL_OK;
+}
+
+// The per-length launches (queued first) on the plan's streams and `main`
+// (the persistent kernel) on the caller's stream, joined back into it.
+template <class F, class G>
+hankel_status run_forked_with(hankel_plan_s* p, const std::vector<hk::RealLaunch>& launches, cudaStream_t st,
+                              F launch, G main) {
+    cudaError_t e;
+    if (launches.empty() || p->streams.empty()) {
+        for (auto& lc : launches)
+            if ((e = launch(lc, st)) != cudaSuccess) return cuda_fail(e, "kernel launch");
+        if ((e = main(st)) != cudaSuccess) return cuda_fail(e, "kernel launch");
+        return HANKEL_OK;
+    }
+    const size_t n = std::min(p->streams.size(), launches.size());
+    if ((e = cudaEventRecord(p->events[0], st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    for (size_t i = 0; i < n; ++i)
+        if ((e = cudaStreamWaitEvent(p->streams[i], p->events[0], 0)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamWaitEvent");
+    for (size_t i = 0; i < launches.size(); ++i)
+        if ((e = launch(launches[i], p->streams[i % n])) != cudaSuccess) return cuda_fail(e, "kernel launch");
+    if ((e = main(st)) != cudaSuccess) return cuda_fail(e, "kernel launch");
+    for (size_t i = 0; i < n; ++i) {
+        if ((e = cudaEventRecord(p->events[1 + i], p->streams[i])) != cudaSuccess)
+            return cuda_fail(e, "cudaEventRecord");
+        if ((e = cudaStreamWaitEvent(st, p->events[1 + i], 0)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamWaitEvent");
+    }
     return HANKEL_OK;
 }
 
@@ -1261,36 +1307,13 @@ hankel_status hankel_txv(hankel_plan_t p, const void* h, const void* x, void* y,
                                        (int)(p->flags | (lc.fp64 ? HANKEL_FP64_POWER : 0u)), s);
     };
     if (!p->fast) return run_forked(p, p->fwd_launches, st, fwd);
-    // the per-length launches (queued first) on the plan's streams, the
-    // persistent kernel on the caller's stream, joined back into it
     auto fast = [&](cudaStream_t s) {
         const char* t2 = (const char*)p->d_fast_tw;
         return hk::launch_fast_forward(p->d_fast_items, (int)p->fast_items.size(), p->fast_grid, p->d_fast_jobs, h, x,
                                        y, alpha, t2, t2 + p->fast_tw3, t2 + p->fast_tw5, p->d_fast_slab,
                                        p->d_fast_ctr, p->fast_f64 ? (int)HANKEL_FP64_POWER : 0, s);
     };
-    cudaError_t e;
-    if (p->fwd_launches.empty() || p->streams.empty()) {
-        for (auto& lc : p->fwd_launches)
-            if ((e = fwd(lc, st)) != cudaSuccess) return cuda_fail(e, "kernel launch");
-        if ((e = fast(st)) != cudaSuccess) return cuda_fail(e, "kernel launch");
-        return HANKEL_OK;
-    }
-    const size_t n = std::min(p->streams.size(), p->fwd_launches.size());
-    if ((e = cudaEventRecord(p->events[0], st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
-    for (size_t i = 0; i < n; ++i)
-        if ((e = cudaStreamWaitEvent(p->streams[i], p->events[0], 0)) != cudaSuccess)
-            return cuda_fail(e, "cudaStreamWaitEvent");
-    for (size_t i = 0; i < p->fwd_launches.size(); ++i)
-        if ((e = fwd(p->fwd_launches[i], p->streams[i % n])) != cudaSuccess) return cuda_fail(e, "kernel launch");
-    if ((e = fast(st)) != cudaSuccess) return cuda_fail(e, "kernel launch");
-    for (size_t i = 0; i < n; ++i) {
-        if ((e = cudaEventRecord(p->events[1 + i], p->streams[i])) != cudaSuccess)
-            return cuda_fail(e, "cudaEventRecord");
-        if ((e = cudaStreamWaitEvent(st, p->events[1 + i], 0)) != cudaSuccess)
-            return cuda_fail(e, "cudaStreamWaitEvent");
-    }
-    return HANKEL_OK;
+    return run_forked_with(p, p->fwd_launches, st, fwd, fast);
 }
 
 hankel_status hankel_txv_host(hankel_plan_t p, const void* h, const void* x, void* y, void* alpha,
@@ -1418,10 +1441,18 @@ hankel_status hankel_txv_backward(hankel_plan_t p, const void* grad_y, const voi
     if (!p->real_path) return hk::general_backward(p->gen, grad_y, h, x, grad_h, grad_x, st, g_err);
     const bool dbl = is_double(p->dtype);
     const int stored = (p->flags & HANKEL_STORE_SPECTRA) ? 1 : 0;
-    return run_forked(p, p->bwd_launches, st, [&](const hk::RealLaunch& lc, cudaStream_t s) {
+    auto bwd = [&](const hk::RealLaunch& lc, cudaStream_t s) {
         return hk::launch_real_backward(dbl, lc, p->d_bwd, grad_y, h, x, grad_h, grad_x, p->d_tw, p->d_ws,
                                         (int)(p->flags | (lc.fp64 ? HANKEL_FP64_POWER : 0u)), stored, s);
-    });
+    };
+    if (!p->fast_bwd) return run_forked(p, p->bwd_launches, st, bwd);
+    auto fast = [&](cudaStream_t s) {
+        const char* t2 = (const char*)p->d_fast_tw;
+        return hk::launch_fast_backward(p->d_fast_items, (int)p->fast_items.size(), p->fast_grid, p->d_fast_jobs,
+                                        grad_y, h, x, grad_h, grad_x, t2, t2 + p->fast_tw3, t2 + p->fast_tw5,
+                                        p->d_fast_slab, p->d_fast_ctr, s);
+    };
+    return run_forked_with(p, p->bwd_launches, st, bwd, fast);
 }
 
 hankel_status hankel_plan_query(hankel_plan_t p, hankel_plan_info* info) {

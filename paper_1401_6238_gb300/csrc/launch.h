@@ -36,7 +36,8 @@ int stage_twiddle_count(const FftPlan& P);
 // persistent forward kernel of fast_path.cu: its FFT lengths, jobs per item
 // and launch (t2, t3, t5 = the w_4096^e, w_3072^e, w_5120^e tables; slab =
 // grid x fast_slab_bytes(L) bytes for the longest length L of the items;
-// ctr = two zeroed ints; flags: HANKEL_FP64_POWER when some job's fA or fB
+// ctr = four zeroed ints (the forward's two, the adjoint's two); flags:
+// HANKEL_FP64_POWER when some job's fA or fB
 // asks for FP64 spectrum powers)
 bool fast_length_ok(int L);
 int fast_length(int64_t d);
@@ -47,6 +48,11 @@ size_t fast_slab_bytes(int L);
 cudaError_t launch_fast_forward(const FastItem* items, int nitems, int grid, const FastJob* jobs, const void* h,
                                 const void* x, void* y, void* alpha, const void* t2, const void* t3, const void* t5,
                                 void* slab, int* ctr, int flags, cudaStream_t st);
+// the persistent adjoint over the same items and jobs (gradients of a real
+// loss through y; gy laid out as y, gh / gx as h / x, either may be null)
+cudaError_t launch_fast_backward(const FastItem* items, int nitems, int grid, const FastJob* jobs, const void* gy,
+                                 const void* h, const void* x, void* gh, void* gx, const void* t2, const void* t3,
+                                 const void* t5, void* slab, int* ctr, cudaStream_t st);
 size_t real_launch_smem(bool dbl, const RealLaunch& lc);
 bool fft_factor(int L, FftPlan* P);
 void set_last_error(const std::string& msg);

@@ -272,3 +272,95 @@ def test_bin_policy_routes_a_bin_to_the_per_length_launches(dev, bin_policy):
     assert info1["launches"] > 1
     check(b, y0, a0)
     check(b, y1, a1)
+
+
+# ------------------------------------------------------------- the adjoint
+
+def run_grads(b, g, dev, want_h=True, want_x=True, calls=1, flags=hk.SAME_X, fill=float("nan")):
+    plan = hk.Plan(hk.batch_descs(b), hk.R32, flags)
+    H = torch.tensor(b.h, dtype=torch.float32, device=dev)
+    X = torch.tensor(b.x, dtype=torch.float32, device=dev)
+    G = torch.tensor(g, dtype=torch.float32, device=dev)
+    outs = []
+    for _ in range(calls):
+        gh = torch.full_like(H, fill) if want_h else None
+        gx = torch.full_like(X, fill) if want_x else None
+        plan.backward(G, H, X, gh, gx)
+        torch.cuda.synchronize()
+        outs.append((gh.cpu().numpy().astype(np.float64) if want_h else None,
+                     gx.cpu().numpy().astype(np.float64) if want_x else None))
+    plan.close()
+    return outs
+
+
+def check_grads(b, g, gh, gx, tol=TOL32):
+    for i in range(len(b)):
+        m, n, h, x = b.tensor(i)
+        rh, rxs = oracle.fast_grads(h, [x] * (m - 1), [n] * m, g[b.y_off[i]: b.y_off[i] + n])
+        if gh is not None:
+            got = gh[b.h_off[i]: b.h_off[i] + h.size]
+            e = np.max(np.abs(got - rh.real)) / np.max(np.abs(rh.real))
+            assert e <= tol, ("grad_h", i, m, n, e)
+        if gx is not None:
+            ref = sum(r.real for r in rxs)
+            e = np.max(np.abs(gx[b.x_off[i]: b.x_off[i] + n] - ref)) / np.max(np.abs(ref))
+            assert e <= tol, ("grad_x", i, m, n, e)
+
+
+def upstream(b, seed):
+    return np.random.default_rng(seed).standard_normal(b.y_len)
+
+
+@pytest.mark.parametrize("L", FAST_LENGTHS)
+def test_adjoint_every_length(dev, L):
+    shapes = shapes_for_length(L, [2, 3, 4, 5])
+    b = scaled_tensors(shapes, seed=200 + L)
+    g = upstream(b, L)
+    (gh, gx), = run_grads(b, g, dev)
+    check_grads(b, g, gh, gx)
+
+
+def test_adjoint_high_orders_and_odd_counts(dev):
+    # orders 6..8 and an odd number of tensors per length (a tensor without a
+    # partner, padding slots in the warps of short lengths)
+    shapes = [(6, 50), (7, 40), (8, 30), (6, 300), (7, 250), (8, 200), (3, 17), (4, 800)]
+    b = scaled_tensors(shapes, seed=210)
+    g = upstream(b, 11)
+    (gh, gx), = run_grads(b, g, dev)
+    check_grads(b, g, gh, gx)
+
+
+def test_adjoint_one_gradient_at_a_time(dev):
+    # one output only; the other buffer is not passed, and the gaps between
+    # segments keep their fill
+    b = wl.batched_square(count=65, seed=212, n_lo=16, n_hi=1024)
+    g = upstream(b, 12)
+    fill = -3.5
+    (gh, _), = run_grads(b, g, dev, want_x=False, fill=fill)
+    (_, gx), = run_grads(b, g, dev, want_h=False, fill=fill)
+    check_grads(b, g, gh, None)
+    check_grads(b, g, None, gx)
+    covered = np.zeros(gh.size, bool)
+    for i in range(len(b)):
+        covered[b.h_off[i]: b.h_off[i] + b.orders[i] * (b.dims[i] - 1) + 1] = True
+    assert np.all(gh[~covered] == fill)
+
+
+def test_adjoint_mixed_with_longer_lengths_and_repeat(dev):
+    # generating lengths above 5120 take the per-length adjoint in the same
+    # call; repeated calls give the same bits (the counter re-arms)
+    shapes = [(5, 1000), (4, 1300), (3, 2000), (3, 700), (4, 300), (3, 40), (2, 2561), (5, 1024)]
+    b = scaled_tensors(shapes, seed=213)
+    g = upstream(b, 13)
+    outs = run_grads(b, g, dev, calls=3)
+    for gh, gx in outs[1:]:
+        np.testing.assert_array_equal(gh, outs[0][0])
+        np.testing.assert_array_equal(gx, outs[0][1])
+    check_grads(b, g, outs[0][0], outs[0][1])
+
+
+def test_adjoint_benchmark_shapes(dev):
+    b = wl.batched_square(count=400, seed=214, orders=(3, 4, 5), n_lo=16, n_hi=1024)
+    g = upstream(b, 14)
+    (gh, gx), = run_grads(b, g, dev)
+    check_grads(b, g, gh, gx)

@@ -169,6 +169,7 @@ typedef struct hankel_plan_info {
     int64_t x_elems;
     int64_t y_elems;
     int64_t fp64_power_tensors; /* tensors whose spectrum power is formed in FP64 */
+    int64_t backward_launches;  /* kernel launches per hankel_txv_backward() (real path; else 0) */
 } hankel_plan_info;
 
 /*

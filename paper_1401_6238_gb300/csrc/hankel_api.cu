@@ -1483,6 +1483,7 @@ hankel_status hankel_plan_query(hankel_plan_t p, hankel_plan_info* info) {
         info->distinct_lengths = (int64_t)p->tw_off.size();
         info->workspace_bytes = (int64_t)p->ws_bytes;
         info->fp64_power_tensors = p->fp64_tensors;
+        info->backward_launches = (int64_t)p->bwd_launches.size() + (p->fast_bwd ? 1 : 0);
     } else {
         hk::general_info(p->gen, &info->jobs, &info->launches, &info->distinct_lengths, &info->workspace_bytes);
     }

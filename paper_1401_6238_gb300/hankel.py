@@ -40,7 +40,7 @@ MDESC_DTYPE = np.dtype([("m", np.int32), ("levels", np.int32), ("n", np.int32, (
 class PlanInfo(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in
                 ("count", "jobs", "launches", "distinct_lengths", "max_length", "sum_length", "workspace_bytes",
-                 "h_elems", "x_elems", "y_elems", "fp64_power_tensors")]
+                 "h_elems", "x_elems", "y_elems", "fp64_power_tensors", "backward_launches")]
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}

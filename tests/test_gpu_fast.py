@@ -361,6 +361,9 @@ def test_adjoint_mixed_with_longer_lengths_and_repeat(dev):
 
 def test_adjoint_benchmark_shapes(dev):
     b = wl.batched_square(count=400, seed=214, orders=(3, 4, 5), n_lo=16, n_hi=1024)
+    plan = hk.Plan(hk.batch_descs(b), hk.R32, hk.SAME_X)
+    assert plan.info["backward_launches"] == 1  # the persistent adjoint alone
+    plan.close()
     g = upstream(b, 14)
     (gh, gx), = run_grads(b, g, dev)
     check_grads(b, g, gh, gx)

@@ -183,6 +183,14 @@ typedef struct hankel_plan_info {
  * by a cost model, the same for every call), groups tensors into jobs and
  * kernel launches, builds FP64-generated twiddle tables on the current device
  * and allocates workspace.  Synchronous.
+ * FP32 real tensors with one vector (HANKEL_SAME_X, square) and d <= 5120,
+ * without HANKEL_STORE_SPECTRA, HANKEL_ONE_PER_LAUNCH or
+ * HANKEL_ANTICIRCULANT, run instead in one persistent launch per
+ * hankel_txv (and per hankel_txv_backward, unless their h or x regions
+ * overlap or some of them form FP64 powers) at the shortest length >= d of
+ * 16 2^k and 12 2^k (32 .. 4096) and 5120; hankel_set_bin_policy can move a
+ * length bin back to the per-length launches.  Longer tensors that exceed
+ * one block's shared memory run each transform on a thread-block cluster.
  * Errors: EINVAL for m out of range, a non-positive size, negative offsets,
  * a length beyond the supported maximum; ENOMEM; ECUDA.
  */

@@ -639,6 +639,39 @@ __global__ void __launch_bounds__(BLOCK, HK_FAST_MIN_BLOCKS)
 // from the partner thread's slab), Q formed in registers and transformed,
 // its first pass (radix R, no twiddles) from the same registers.  Five
 // transforms per pair, spectra never leave the block.
+// The adjoint spectrum on the thread's bins b + s NB, times 2^m L:
+// q_s = 2G X'^{m-1} + i (m-1) conj(2H) 2G X'^{m-2} with 2H, X' = 2X from U
+// (v: U on the bins; U_{L-k} from the mirror lane as in the forward product)
+// and 2G_A or 2G_B from the slab (own slot s, the mirror bin's slot of the
+// partner thread, gp); every factor 2 and the 1/L are one power-of-two scale
+// 2^-m / L on the stored gradients.  E: the exponent m - 2 at compile time
+// (1 .. 3), 0 for the run-time one.
+template <int R, int E>
+__device__ __forceinline__ void adj_bins(const cx<float>* v, cx<float>* q, const cx<float>* gs, const cx<float>* gp,
+                                         int src, bool self0, bool B, int m, int e) {
+    const float fm = (float)(m - 1);
+    cx<float> prev = v[0];
+#pragma unroll
+    for (int s = 0; s < R; ++s) {
+        const cx<float> o = v[R - 1 - s];
+        cx<float> uc = mk<float>(__shfl_sync(0xffffffffu, o.x, src), __shfl_sync(0xffffffffu, o.y, src));
+        uc = sel(self0, prev, uc);  // U_{L-k}
+        prev = o;
+        const cx<float> a = v[s];
+        // conj(2H) = conj(U_k + conj U_{L-k}), 2X = -i (U_k - conj U_{L-k})
+        const cx<float> H2c = mk<float>(a.x + uc.x, uc.y - a.y);
+        const cx<float> X2 = mk<float>(a.y + uc.y, uc.x - a.x);
+        const cx<float> Gk = gs[s * BLOCK];
+        const cx<float> Gc = gp[(self0 ? (R - s) % R : R - 1 - s) * BLOCK];  // G_{L-k}
+        // 2G_A = G_k + conj G_{L-k}, 2G_B = -i (G_k - conj G_{L-k})
+        const cx<float> G2 = B ? mk<float>(Gk.y + Gc.y, Gc.x - Gk.x) : mk<float>(Gk.x + Gc.x, Gk.y - Gc.y);
+        const cx<float> gx2 = E == 0 ? times_pow<0>(G2, X2, e) : times_pow<E>(G2, X2, E);  // 2G X'^{m-2}
+        const cx<float> qh = cmul(gx2, X2);
+        const cx<float> qx = cmul(H2c, gx2);
+        q[s] = mk<float>(qh.x - fm * qx.y, qh.y + fm * qx.x);
+    }
+}
+
 template <int L>
 __device__ __noinline__ int run_adj_item(int first, int staged, int next) {
     constexpr int R = rlast(L), T = nthr(L), Q = L / R, GS = gslots(L);
@@ -708,35 +741,17 @@ __device__ __noinline__ int run_adj_item(int first, int staged, int next) {
             cur ^= 1;
         }
         last_pass<L, R>(v, buf(cur), b, tw);
-        // Q on the thread's bins
-        cx<float> prev = v[0];
-#pragma unroll
-        for (int s = 0; s < R; ++s) {
-            const cx<float> o = v[R - 1 - s];
-            cx<float> uc = mk<float>(__shfl_sync(0xffffffffu, o.x, src), __shfl_sync(0xffffffffu, o.y, src));
-            uc = sel(self0, prev, uc);  // U_{L-k}
-            prev = o;
-            const cx<float> a = v[s];
-            // H = (U_k + conj U_{L-k}) / 2, X = -i (U_k - conj U_{L-k}) / 2
-            const cx<float> Hk = mk<float>(0.5f * (a.x + uc.x), 0.5f * (a.y - uc.y));
-            const cx<float> X = mk<float>(0.5f * (a.y + uc.y), 0.5f * (uc.x - a.x));
-            const cx<float> Gk = gs[s * BLOCK];
-            const cx<float> Gc = gp[(self0 ? (R - s) % R : R - 1 - s) * BLOCK];  // G_{L-k}
-            // G_A = (G_k + conj G_{L-k}) / 2, G_B = -i (G_k - conj G_{L-k}) / 2
-            const cx<float> Gt = B ? mk<float>(0.5f * (Gk.y + Gc.y), 0.5f * (Gc.x - Gk.x))
-                                   : mk<float>(0.5f * (Gk.x + Gc.x), 0.5f * (Gk.y - Gc.y));
-            cx<float> gx2 = Gt;  // G X^{m-2}
-            const int e = m - 2;
-            if (e & 1) gx2 = cmul(gx2, X);
-            if (e & 6) {
-                const cx<float> X2 = cmul(X, X);
-                if (e & 2) gx2 = cmul(gx2, X2);
-                if (e & 4) gx2 = cmul(gx2, cmul(X2, X2));
+        // Q on the thread's bins, times 2^m L (the scale is applied on store)
+        const int e = m - 2;
+        if constexpr (T >= 32) {
+            switch (e) {
+                case 1: adj_bins<R, 1>(v, q, gs, gp, src, self0, B, m, e); break;
+                case 2: adj_bins<R, 2>(v, q, gs, gp, src, self0, B, m, e); break;
+                case 3: adj_bins<R, 3>(v, q, gs, gp, src, self0, B, m, e); break;
+                default: adj_bins<R, 0>(v, q, gs, gp, src, self0, B, m, e); break;
             }
-            const cx<float> qh = cmul(gx2, X);                                        // G X^{m-1}
-            const cx<float> qx = cmul(mk<float>(Hk.x, -Hk.y), gx2);                   // conj(H) G X^{m-2}
-            const float fm = (float)(m - 1) * invL;
-            q[s] = mk<float>(qh.x * invL - qx.y * fm, qh.y * invL + qx.x * fm);      // qh / L + i (m-1) qx / L
+        } else {
+            adj_bins<R, 0>(v, q, gs, gp, src, self0, B, m, e);
         }
         // fft(Q): first pass from registers, the power-of-two passes, the last
         // one storing the gradients
@@ -764,6 +779,7 @@ __device__ __noinline__ int run_adj_item(int first, int staged, int next) {
         const int n = B ? J.nB : J.nA, d = B ? J.dB : J.dA;
         float* gh = c.gh ? c.gh + (B ? J.hB : J.hA) : nullptr;
         float* gx = c.gx ? c.gx + (B ? J.xB : J.xA) : nullptr;
+        const float sc = ldexpf(invL, -m);
 #pragma unroll 1
         for (int j = 0; j < IT; ++j) {
             const int bl = t + T * j;
@@ -774,8 +790,8 @@ __device__ __noinline__ int run_adj_item(int first, int staged, int next) {
                 for (int s = 0; s < QA; ++s) {
                     const int i0 = bl + s * NBL;
                     const int jh = i0 == 0 ? 0 : L - i0;
-                    if (gh != nullptr && jh < d) gh[jh] = w[s].x;
-                    if (gx != nullptr && i0 < n) gx[i0] = w[s].y;
+                    if (gh != nullptr && jh < d) gh[jh] = w[s].x * sc;
+                    if (gx != nullptr && i0 < n) gx[i0] = w[s].y * sc;
                 }
             }
         }

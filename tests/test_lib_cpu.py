@@ -2,6 +2,7 @@
 every entry point include/hankel.h declares, its planner picks valid FFT
 lengths, and descriptor validation rejects bad input with a status code."""
 
+import ctypes
 import os
 import re
 
@@ -39,6 +40,20 @@ def test_desc_layout_matches_header():
     assert hk.DESC_DTYPE.itemsize == 152
     assert hk.DESC_DTYPE.fields["h_off"][1] == 72
     assert hk.DESC_DTYPE.fields["y_off"][1] == 144
+
+
+def test_plan_info_mirrors_header():
+    # the ctypes mirror of hankel_plan_info lists the header's fields in order
+    # (all int64): a field added on one side only would shift every later one
+    import re
+    with open(os.path.join(ROOT, "include", "hankel.h")) as f:
+        text = f.read()
+    body = re.search(r"typedef struct hankel_plan_info \{(.*?)\} hankel_plan_info;", text, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)  # comments out
+    fields = re.findall(r"int64_t\s+(\w+)\s*;", body)
+    assert len(fields) == len(re.findall(r";", body))  # every member is an int64_t
+    assert [f for f, _ in hk.PlanInfo._fields_] == fields
+    assert all(t is ctypes.c_int64 for _, t in hk.PlanInfo._fields_)
 
 
 def smooth(L):
